@@ -1,0 +1,303 @@
+"""Benchmark of the HP genotype-phenotype map hot path on GB300.
+
+One step = the whole map path over the full 3x3x3 sequence space (2^27 HP
+sequences x 103,346 directed conformations): phenotype map, designability,
+robustness / phi_del numerators and neutral components.  Metric: sequence x
+conformation evaluations per second (and sequences per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (the only reference this project has:
+the paper ships no runnable code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HP seq×struct evals/s & sequences/s (3x3x3, 6x6); learned-pruned vs plain"
+DIMS = (3, 3, 3)
+WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformations (51,704 classes)"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(dims, budget_s: float = 12.0):
+    """The oracle as it stands, on all host cores, on a bounded seeded sample of the workload."""
+    import oracle
+    from paper_2008_05612_gb300 import inputs
+
+    b = oracle.Box(dims)
+    cores = os.cpu_count() or 1
+    n = 64
+    ids = inputs.sample_ids(b.N, n, seed=41)
+    t = time.perf_counter()
+    b.phenotypes(ids, nthreads=cores)
+    dt = time.perf_counter() - t
+    n = int(max(64, min(200000, n * budget_s / max(dt, 1e-3))))
+    ids = inputs.sample_ids(b.N, n, seed=43)
+    t = time.perf_counter()
+    b.phenotypes(ids, nthreads=cores)
+    dt = time.perf_counter() - t
+    evals = n * b.S_dir
+    return {"value": evals / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} seeded 3x3x3 sequences x {b.S_dir} conformations (direct contact sums), {dt:.1f} s",
+            "sequences_per_s": n / dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2008_05612_gb300 import inputs
+
+    b = oracle.Box(DIMS)
+    cores = os.cpu_count() or 1
+    n = 2048 * max(1, cores // 8)
+    ids = inputs.sample_ids(b.N, n, seed=47)
+    for _ in range(args.warmup):
+        b.phenotypes(ids[:256], nthreads=cores)
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        b.phenotypes(inputs.sample_ids(b.N, n, seed=100 + k), nthreads=cores)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    evals = n * b.S_dir * args.steps
+    v = evals / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic (exhaustive sequence space, seeded sample)",
+            "config": {"workload": WORKLOAD + f"; oracle timed on a seeded sample of {n} sequences per step"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} seeded sequences per step"},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sequences_per_s": n * args.steps / tot}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import __graft_entry__
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    import paper_2008_05612_gb300 as hp
+
+    s = hp.Structs(DIMS)
+    N, S, Sdir = s.N, s.S, s.S_dir
+    nseq = 1 << N
+    stream = torch.cuda.current_stream()
+    phen = torch.empty(nseq, dtype=torch.int32, device="cuda")
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        hp.phenotype_map(s, 0, nseq, out=phen)
+        if ev is not None:
+            ev[1].record(stream)
+        hist = hp.designability(phen, S)
+        neutral, to_del = hp.robustness(phen, N, S)
+        label, ncomp = hp.neutral_components(phen, N, S)
+        return hist, neutral, to_del, label, ncomp
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region (inputs resident: the structure tables are on the device)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            out = step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    map_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_step = ms / args.steps
+    evals_step = nseq * Sdir
+    value = world * evals_step / (ms_step * 1e-3)
+    hist = out[0].cpu().numpy()
+
+    # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
+    h_phen = torch.empty(nseq, dtype=torch.int32, pin_memory=True)
+    h_label = torch.empty(nseq, dtype=torch.int32, pin_memory=True)
+    h_rec = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(2, min(args.steps, 3))
+    e0.record(stream)
+    d2h = 0
+    for _ in range(e2e_steps):
+        hp.phenotype_map(s, 0, nseq, out=phen)
+        hist_d = hp.designability(phen, S)
+        neutral, to_del = hp.robustness(phen, N, S)
+        label, ncomp = hp.neutral_components(phen, N, S)
+        h_phen.copy_(phen, non_blocking=True)
+        h_label.copy_(label, non_blocking=True)
+        hh = hist_d.to("cpu", non_blocking=True)
+        hn = neutral.to("cpu", non_blocking=True)
+        hd = to_del.to("cpu", non_blocking=True)
+        hc = ncomp.to("cpu", non_blocking=True)
+        d2h = (h_phen.numel() + h_label.numel()) * 4 + (hh.numel() + hn.numel() + hd.numel() + hc.numel()) * 8
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    del h_rec
+
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_ops = 128 * 152 * sm_max * 1e6  # lane-instructions issued per second: 4 SMSPs x 32 lanes per SM per clock
+    map_avg_ms = float(np.mean(map_ms))
+    achieved = evals_step / (map_avg_ms * 1e-3)  # 1 packed lane-op (half an add + half a max) per evaluation
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic (exhaustive: every sequence of the box; fold library enumerated by the library)",
+        "config": {"workload": WORKLOAD, "box": "3x3x3", "sequences": nseq, "conformations": Sdir, "classes": S,
+                   "step": "phenotype map + designability + robustness + neutral components",
+                   "l2": "map and labels (512 MB each) exceed L2 every step; the 7 MB conformation table stays resident by design",
+                   "parallelism": "replicas" if world == 1 else f"replicas x{world}"},
+        "sequences_per_s": world * nseq / (ms_step * 1e-3),
+        "map_ms": map_avg_ms,
+        "map_evals_per_s": achieved,
+        "fold_fraction": float(1.0 - hist[S] / nseq),
+        "gpu_launches": args.steps * 8,
+        "e2e": {"value": world * evals_step / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(d2h),
+                "note": "public Python API; outputs copied to pinned host memory inside the timed region; the only input "
+                        "is the sequence range (no per-step input data)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "lane-ops/s",
+                     "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "phenotype_kernel<6,256>",
+                     "note": "1 packed 32-bit lane-op per evaluation (16-bit add + max, two sequences per op) vs the issue "
+                             "limit 128 lane-ops/clk/SM x 152 SMs x max SM clock"},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(DIMS)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,121 @@
+/*
+ * hp_gpmap.h -- C ABI of the GB300 HP-model genotype-phenotype map library.
+ *
+ * Method: arXiv 2008.05612 (Owen), "GPU accelerated enumeration and
+ * exploration of model genotype-phenotype maps for protein folding".
+ *
+ * Conventions used by every entry point
+ *   - A sequence (genotype) of N residues is a 64-bit id g; bit i of g is
+ *     residue i, 1 = H (hydrophobic), 0 = P (polar).
+ *   - Energies are the Li et al. values of Table 1 scaled by 10 to integers
+ *     (Section 2.2): HH = -23, HP = PH = -10, PP = 0, summed over contacts as
+ *     in Eq. 1 (lattice neighbours that are not chain neighbours).
+ *   - A conformation is a Hamiltonian path of the box (a compact
+ *     self-avoiding walk, Section 2.1) modulo the box's rotations and
+ *     reflections G; a class (the phenotype) is a conformation modulo G and
+ *     chain reversal.  Every conformation competes; a sequence folds to the
+ *     class of the unique lowest-energy conformation and otherwise gets the
+ *     deleterious phenotype -1 (Section 2.1, energy-threshold paragraph, with
+ *     threshold 1 in integer units as in Appendix C).
+ *   - Class ids are ranks of class representatives: the representative is
+ *     the lexicographically smallest tuple (site(r_0), ..., site(r_{N-1})),
+ *     site = x + Lx*(y + Ly*z), over G and both directions.
+ *   - Device pointers are plain CUDA device addresses owned by the caller;
+ *     `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     is stream-ordered and returns as soon as its work is enqueued, except
+ *     where stated.  No call aborts the process; each returns an hp_status
+ *     and leaves a message for hp_last_error().
+ */
+#ifndef HP_GPMAP_H
+#define HP_GPMAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HP_OK = 0,
+  HP_EINVAL = -1,        /* bad argument (null pointer, size, shape) */
+  HP_ENOMEM = -2,        /* host or device allocation failed */
+  HP_ECUDA = -3,         /* a CUDA runtime call failed */
+  HP_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
+  HP_EUNSUPPORTED = -5   /* valid request this build does not implement */
+} hp_status;
+
+typedef struct hp_structs hp_structs; /* opaque fold library, library-owned */
+
+/* Enumerate the fold library of a box (Section 2.1: all compact
+ * self-avoiding walks), reduced by G and reversal.
+ *   ndim: 2 or 3; dims[0..ndim-1]: side lengths (>= 1), N = product <= 40.
+ *   out:  receives a new library handle; free it with hp_structs_free.
+ * Host-only call.  Fails with HP_EINVAL for bad shapes, HP_EUNSUPPORTED for
+ * N > 40, HP_ENOMEM if the library does not fit in host memory. */
+int hp_enumerate_structures(int ndim, const int32_t dims[3], hp_structs** out);
+
+/* Sizes of a library: N residues, S classes (phenotypes), S_dir directed
+ * conformations (S <= S_dir <= 2S), C contacts per conformation (the same for
+ * every compact walk).  Any output pointer may be NULL. */
+int hp_structs_info(const hp_structs* s, int32_t* N, int32_t* S, int32_t* S_dir, int32_t* C);
+
+/* Copy the library out to host memory (any pointer may be NULL):
+ *   coords:     S_dir x N site indices, conformations in canonical order
+ *               (by class, canonical orientation first);
+ *   contacts:   S_dir x C x 2 residue indices (i < j) of each contact,
+ *               sorted by (i, j);
+ *   conf_class: S_dir class ids. */
+int hp_structs_export(const hp_structs* s, uint8_t* coords, uint8_t* contacts, int32_t* conf_class);
+
+void hp_structs_free(hp_structs* s);
+
+/* Ground-state phenotype of every sequence id in [seq_begin, seq_begin +
+ * seq_count) (Section 2.1; Appendix C kernel semantics with threshold 1).
+ *   gap_threshold: minimum energy gap between the lowest and second-lowest
+ *                  conformation for a sequence to fold; only 1 (strict
+ *                  uniqueness) is implemented, others give HP_EUNSUPPORTED.
+ *   d_phen:        device int32[seq_count]; d_phen[k] = phenotype of
+ *                  seq_begin + k: class id, or -1.
+ *   d_argmin_aux:  optional device int32[seq_count] (NULL to skip): class of
+ *                  the lowest-index conformation reaching the minimum energy,
+ *                  tied or not (training labels for the learned proposal).
+ * seq_begin + seq_count must not exceed 2^N.  Allocates a small stream-
+ * ordered scratch block (work counter and error word) per call. */
+int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_t seq_count, int32_t gap_threshold,
+                     int32_t* d_phen, int32_t* d_argmin_aux, void* stream);
+
+/* Designability (Section 2.3): d_hist[p] = #{k : d_phen[k] = p} for
+ * p in [0, S), d_hist[S] = #{k : d_phen[k] = -1}.
+ *   d_phen: device int32[count], entries in [-1, S); d_hist: device
+ *   uint64[S + 1], overwritten.  Entries outside [-1, S) set HP_EINVAL at the
+ *   next synchronising call of this library (they are counted nowhere). */
+int hp_designability(const int32_t* d_phen, uint64_t count, int32_t S, uint64_t* d_hist, void* stream);
+
+/* Numerators of Eq. 2 for p = q, over a FULL map of 2^N sequences (K = 2, so
+ * every genotype has (K-1)L = N single-flip neighbours):
+ *   d_neutral[p] = sum over g with P(g) = p of #{i : P(g xor 2^i) = p}
+ *   d_to_del[p]  = sum over g with P(g) = p of #{i : P(g xor 2^i) = -1}
+ * for p in [0, S); index S stands for the deleterious phenotype.  Robustness
+ * rho_p = d_neutral[p] / (N * N_p) and phi_del = d_to_del[p] / (N * N_p).
+ *   d_phen: device int32[2^N]; d_neutral, d_to_del: device uint64[S + 1]. */
+int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64_t* d_neutral, uint64_t* d_to_del,
+                  void* stream);
+
+/* Neutral networks (Section 1; never computed in the paper): connected
+ * components of the graph whose vertices are sequences with P(g) != -1 and
+ * whose edges join g and g xor 2^i when P is equal.
+ *   d_phen:  device int32[2^N], N <= 31;
+ *   d_label: device int32[2^N]; d_label[g] = smallest id in g's component,
+ *            -1 where P(g) = -1;
+ *   d_ncomp: device uint64[S]; number of components of each phenotype. */
+int hp_neutral_components(const int32_t* d_phen, int32_t N, int32_t S, int32_t* d_label, uint64_t* d_ncomp,
+                          void* stream);
+
+/* Thread-local text of the last failure in this library (never NULL). */
+const char* hp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HP_GPMAP_H */

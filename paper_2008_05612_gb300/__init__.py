@@ -1,0 +1,176 @@
+"""GB300 HP-model genotype-phenotype map (arXiv 2008.05612), Python binding.
+
+Every function here only marshals arguments for the C ABI declared in
+include/hp_gpmap.h; all computation runs in libhp_gpmap.so (host enumeration
+in C++, everything per sequence in CUDA kernels for sm_103a).  PyTorch only
+provides device memory and streams.  There is no CPU fallback: if the library
+is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libhp_gpmap.so")
+
+HP_OK, HP_EINVAL, HP_ENOMEM, HP_ECUDA, HP_ETIMEOUT, HP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+_STATUS = {0: "HP_OK", -1: "HP_EINVAL", -2: "HP_ENOMEM", -3: "HP_ECUDA", -4: "HP_ETIMEOUT", -5: "HP_EUNSUPPORTED"}
+
+# every symbol the header declares (checked by the CPU test-suite)
+EXPORTS = (
+    "hp_enumerate_structures", "hp_structs_info", "hp_structs_export", "hp_structs_free",
+    "hp_phenotype_map", "hp_designability", "hp_robustness", "hp_neutral_components", "hp_last_error",
+)
+
+_lib = None
+_lock = threading.Lock()
+
+
+class HPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libhp_gpmap.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhp_gpmap.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+        L.hp_enumerate_structures.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.hp_structs_info.argtypes = [vp, vp, vp, vp, vp]
+        L.hp_structs_export.argtypes = [vp, vp, vp, vp]
+        L.hp_structs_free.argtypes = [vp]
+        L.hp_structs_free.restype = None
+        L.hp_phenotype_map.argtypes = [vp, u64, u64, i32, vp, vp, vp]
+        L.hp_designability.argtypes = [vp, u64, i32, vp, vp]
+        L.hp_robustness.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.hp_neutral_components.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.hp_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name != "hp_structs_free" and name != "hp_last_error":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != HP_OK:
+        raise HPError(rc, lib().hp_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Structs:
+    """Fold library of a box (hp_enumerate_structures)."""
+
+    def __init__(self, dims):
+        dims = tuple(int(d) for d in dims)
+        if len(dims) not in (2, 3):
+            raise ValueError("dims must have 2 or 3 entries")
+        self.dims = dims
+        d = (ctypes.c_int32 * 3)(*(list(dims) + [1] * (3 - len(dims))))
+        h = ctypes.c_void_p()
+        _check(lib().hp_enumerate_structures(len(dims), d, ctypes.byref(h)))
+        self._h = h
+        vals = [ctypes.c_int32() for _ in range(4)]
+        _check(lib().hp_structs_info(h, *[ctypes.byref(v) for v in vals]))
+        self.N, self.S, self.S_dir, self.C = (v.value for v in vals)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.hp_structs_free(h)
+            self._h = None
+
+    def export(self):
+        """(coords S_dir x N uint8, contacts S_dir x C x 2 uint8, conf_class S_dir int32)"""
+        coords = np.zeros((self.S_dir, self.N), dtype=np.uint8)
+        contacts = np.zeros((self.S_dir, max(self.C, 1), 2), dtype=np.uint8)
+        cls = np.zeros(self.S_dir, dtype=np.int32)
+        _check(lib().hp_structs_export(self._h, coords.ctypes.data_as(ctypes.c_void_p),
+                                       contacts.ctypes.data_as(ctypes.c_void_p), cls.ctypes.data_as(ctypes.c_void_p)))
+        return coords, contacts[:, : self.C], cls
+
+
+def phenotype_map(structs: Structs, begin: int = 0, count: int | None = None, out=None, aux=None,
+                  gap_threshold: int = 1, stream=None):
+    """Phenotype of every id in [begin, begin + count) into a device int32 tensor (hp_phenotype_map)."""
+    import torch
+
+    if count is None:
+        count = (1 << structs.N) - begin
+    if out is None:
+        out = torch.empty(count, dtype=torch.int32, device="cuda")
+    if out.numel() < count:
+        raise ValueError("out is smaller than count")
+    paux = _dptr(aux, torch.int32, "aux") if aux is not None else None
+    if aux is not None and aux.numel() < count:
+        raise ValueError("aux is smaller than count")
+    _check(lib().hp_phenotype_map(structs.handle, begin, count, gap_threshold, _dptr(out, torch.int32, "out"), paux,
+                                  _stream_ptr(stream)))
+    return out
+
+
+def designability(phen, S: int, out=None, stream=None):
+    import torch
+
+    if out is None:
+        out = torch.empty(S + 1, dtype=torch.int64, device=phen.device)
+    _check(lib().hp_designability(_dptr(phen, torch.int32, "phen"), phen.numel(), S, _dptr(out, torch.int64, "out"),
+                                  _stream_ptr(stream)))
+    return out
+
+
+def robustness(phen, N: int, S: int, stream=None):
+    """(neutral[S+1], to_del[S+1]) numerators of Eq. 2 over a full 2^N map (hp_robustness)."""
+    import torch
+
+    if phen.numel() != (1 << N):
+        raise ValueError("robustness needs the full map of 2^N sequences")
+    neutral = torch.empty(S + 1, dtype=torch.int64, device=phen.device)
+    to_del = torch.empty(S + 1, dtype=torch.int64, device=phen.device)
+    _check(lib().hp_robustness(_dptr(phen, torch.int32, "phen"), N, S, _dptr(neutral, torch.int64, "neutral"),
+                               _dptr(to_del, torch.int64, "to_del"), _stream_ptr(stream)))
+    return neutral, to_del
+
+
+def neutral_components(phen, N: int, S: int, stream=None):
+    """(label[2^N], ncomp[S]) of the neutral networks (hp_neutral_components)."""
+    import torch
+
+    if phen.numel() != (1 << N):
+        raise ValueError("components need the full map of 2^N sequences")
+    label = torch.empty(1 << N, dtype=torch.int32, device=phen.device)
+    ncomp = torch.empty(S, dtype=torch.int64, device=phen.device)
+    _check(lib().hp_neutral_components(_dptr(phen, torch.int32, "phen"), N, S, _dptr(label, torch.int32, "label"),
+                                       _dptr(ncomp, torch.int64, "ncomp"), _stream_ptr(stream)))
+    return label, ncomp

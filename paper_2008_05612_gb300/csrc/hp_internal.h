@@ -1,0 +1,62 @@
+// Internal declarations shared by the translation units of libhp_gpmap.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hp_gpmap.h"
+
+namespace hp {
+
+constexpr int kMaxN = 40;       // residues per chain
+constexpr int kMaxHalf = 20;    // even (or odd) residues per chain
+constexpr int kMaxSym = 48;     // order of the cube's symmetry group
+
+// Sets the thread-local error text and returns `code`.
+int fail(int code, const std::string& msg);
+int cuda_fail(int err, const char* what);  // err is a cudaError_t
+
+// Per-device copy of a fold library's kernel tables.
+struct DevTables {
+  int device = -1;
+  uint32_t* rec = nullptr;       // S_pad x rec_words contact records
+  int32_t* conf_class = nullptr; // S_dir class ids
+};
+
+}  // namespace hp
+
+// Fold library (opaque in the C ABI).
+struct hp_structs {
+  int ndim = 0;
+  int L[3] = {1, 1, 1};
+  int N = 0;
+  int NE = 0;        // even residues: 0, 2, 4, ...
+  int NO = 0;        // odd residues: 1, 3, 5, ...
+  int C = 0;         // contacts per conformation
+  int nsym = 0;
+  int32_t S = 0;     // classes
+  int32_t S_dir = 0; // directed conformations
+  std::vector<uint8_t> conf;        // S_dir x N sites
+  std::vector<int32_t> conf_class;  // S_dir
+  std::vector<uint8_t> contacts;    // S_dir x C x 2 residues (i < j)
+  // Kernel record of each conformation (rec_words uint32, rec_words odd so a
+  // thread-per-record shared-memory read is conflict-free):
+  //   [k]      for k < NE: contact mask of even residue 2k over odd residues
+  //            (bit j = odd residue 2j+1)
+  //   [NE+b]   for b < 3: bit b of the contact count of each odd residue,
+  //            as a mask over odd residues
+  //   rest     zero padding
+  int rec_words = 0;
+  std::vector<uint32_t> rec;        // S_dir x rec_words
+  std::mutex mu;
+  std::vector<hp::DevTables*> dev;  // lazily uploaded, one entry per device
+};
+
+namespace hp {
+// Upload (once per device) and return the device tables for the current device.
+int device_tables(const hp_structs* s, DevTables** out);
+// Records are padded on the device to a multiple of this many conformations.
+constexpr int kRecPad = 256;
+}  // namespace hp

@@ -1,0 +1,334 @@
+// Reductions of a phenotype map (Section 2.3 of arXiv 2008.05612):
+// designability, the Eq. 2 numerators behind robustness and phi_del, and the
+// neutral networks (connected components of same-phenotype single flips).
+// All three are HBM-bound passes over the int32 map.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "hp_internal.h"
+
+namespace {
+
+constexpr unsigned kErrRange = 4u;     // a map entry outside [-1, S)
+constexpr unsigned kErrUnion = 8u;     // union retries exhausted
+constexpr int kHistThreads = 1024;
+constexpr int kRobTileBits = 14;       // 2^14 ids (64 KB) of the map per CTA
+constexpr int kRobThreads = 512;
+
+// ---------------------------------------------------------------- designability
+
+// Privatised histogram in shared memory, one partial row per CTA.  Entry -1 is
+// by far the most common (95% of 3x3x3 genotypes), so it is counted in a
+// register and added once per warp.
+__global__ void __launch_bounds__(kHistThreads) hist_partial(const int32_t* __restrict__ phen, unsigned long long count,
+                                                             int S, unsigned* __restrict__ partial,
+                                                             unsigned* __restrict__ err, int vec4) {
+  extern __shared__ unsigned bins[];
+  for (int b = threadIdx.x; b <= S; b += blockDim.x) bins[b] = 0u;
+  __syncthreads();
+  unsigned neg = 0, bad = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  auto take = [&](int32_t p) {
+    if (p < 0) {
+      if (p == -1) neg++; else bad = 1;
+    } else if (p < S) {
+      atomicAdd(&bins[p], 1u);
+    } else {
+      bad = 1;
+    }
+  };
+  unsigned long long done = 0;
+  if (vec4) {
+    const int4* v = reinterpret_cast<const int4*>(phen);
+    const unsigned long long nv = count / 4;
+    for (unsigned long long k = t0; k < nv; k += stride) {
+      const int4 q = __ldcs(v + k);
+      take(q.x); take(q.y); take(q.z); take(q.w);
+    }
+    done = nv * 4;
+  }
+  for (unsigned long long k = done + t0; k < count; k += stride) take(__ldcs(phen + k));
+  for (int off = 16; off; off >>= 1) neg += __shfl_xor_sync(0xFFFFFFFFu, neg, off);
+  if ((threadIdx.x & 31) == 0 && neg) atomicAdd(&bins[S], neg);
+  if (bad) atomicOr(err, kErrRange);
+  __syncthreads();
+  unsigned* row = partial + (size_t)blockIdx.x * (S + 1);
+  for (int b = threadIdx.x; b <= S; b += blockDim.x) row[b] = bins[b];
+}
+
+__global__ void hist_sum(const unsigned* __restrict__ partial, int rows, int S, unsigned long long* __restrict__ hist) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > S) return;
+  unsigned long long s = 0;
+  for (int r = 0; r < rows; r++) s += partial[(size_t)r * (S + 1) + b];
+  hist[b] = s;
+}
+
+// fallback for phenotype counts too large for one shared-memory histogram
+__global__ void hist_global(const int32_t* __restrict__ phen, unsigned long long count, int S,
+                            unsigned long long* __restrict__ hist, unsigned* __restrict__ err) {
+  unsigned neg = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) {
+    const int32_t p = phen[k];
+    if (p == -1) neg++;
+    else if (p >= 0 && p < S) atomicAdd(&hist[p], 1ull);
+    else atomicOr(err, kErrRange);
+  }
+  for (int off = 16; off; off >>= 1) neg += __shfl_xor_sync(0xFFFFFFFFu, neg, off);
+  if ((threadIdx.x & 31) == 0 && neg) atomicAdd(&hist[S], (unsigned long long)neg);
+}
+
+// ---------------------------------------------------------------- robustness
+
+// One CTA per tile of 2^kRobTileBits consecutive ids: flips of the low bits are
+// read from shared memory, flips of higher bits from global memory.  Only
+// genotypes with P(g) >= 0 examine their flips; the -1 row follows from the
+// edge identity sum_{P(g)=-1} #{i: P(g^2^i) = -1} = N N_{-1} - sum_{p>=0} to_del[p].
+__global__ void __launch_bounds__(kRobThreads) robustness_tiles(const int32_t* __restrict__ phen, int N, int S,
+                                                                unsigned long long* __restrict__ neutral,
+                                                                unsigned long long* __restrict__ to_del,
+                                                                unsigned long long* __restrict__ negcount,
+                                                                unsigned* __restrict__ err) {
+  extern __shared__ int32_t tile[];
+  const int k = min(N, kRobTileBits);
+  const unsigned long long tsize = 1ull << k;
+  const unsigned long long g0 = (unsigned long long)blockIdx.x << k;
+  for (unsigned long long j = threadIdx.x; j < tsize; j += blockDim.x) tile[j] = __ldcs(phen + g0 + j);
+  __syncthreads();
+  unsigned neg = 0;
+  for (unsigned long long j = threadIdx.x; j < tsize; j += blockDim.x) {
+    const int32_t p = tile[j];
+    if (p < 0) {
+      neg += p == -1;
+      if (p != -1) atomicOr(err, kErrRange);
+      continue;
+    }
+    if (p >= S) {
+      atomicOr(err, kErrRange);
+      continue;
+    }
+    unsigned nn = 0, nd = 0;
+    for (int i = 0; i < k; i++) {
+      const int32_t q = tile[j ^ (1ull << i)];
+      nn += q == p;
+      nd += q < 0;
+    }
+    const unsigned long long g = g0 + j;
+    for (int i = k; i < N; i++) {
+      const int32_t q = __ldg(phen + (g ^ (1ull << i)));
+      nn += q == p;
+      nd += q < 0;
+    }
+    if (nn) atomicAdd(&neutral[p], (unsigned long long)nn);
+    if (nd) atomicAdd(&to_del[p], (unsigned long long)nd);
+  }
+  for (int off = 16; off; off >>= 1) neg += __shfl_xor_sync(0xFFFFFFFFu, neg, off);
+  if ((threadIdx.x & 31) == 0 && neg) atomicAdd(negcount, (unsigned long long)neg);
+}
+
+__global__ void robustness_finish(int N, int S, unsigned long long* __restrict__ neutral,
+                                  unsigned long long* __restrict__ to_del, const unsigned long long* __restrict__ negcount) {
+  __shared__ unsigned long long part[32];
+  unsigned long long s = 0;
+  for (int p = threadIdx.x; p < S; p += blockDim.x) s += to_del[p];
+  for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+    const unsigned long long v = (unsigned long long)N * negcount[0] - t;
+    neutral[S] = v;
+    to_del[S] = v;
+  }
+}
+
+// ---------------------------------------------------------------- components
+
+__global__ void cc_init(const int32_t* __restrict__ phen, unsigned long long total, int S, int32_t* __restrict__ label,
+                        unsigned* __restrict__ err) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int32_t p = phen[g];
+    if (p < -1 || p >= S) atomicOr(err, kErrRange);
+    label[g] = (p >= 0 && p < S) ? (int32_t)g : -1;
+  }
+}
+
+// Root of x: parents always have smaller ids, so the walk terminates.
+__device__ __forceinline__ int32_t cc_find(const int32_t* label, int32_t x) {
+  int32_t par = __ldcg(label + x);
+  while (par != x) {
+    x = par;
+    par = __ldcg(label + x);
+  }
+  return x;
+}
+
+// Lock-free union: hook the larger root under the smaller one with a CAS and
+// retry from the value the CAS saw.  Every failed CAS means another thread
+// linked that root, so the loop makes progress; it is bounded all the same.
+__global__ void cc_hook(const int32_t* __restrict__ phen, int N, int32_t* label, unsigned* __restrict__ err) {
+  const unsigned long long total = 1ull << N;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    if (__ldcg(label + g) < 0) continue;  // deleterious or out of range
+    const int32_t p = __ldg(phen + g);
+    for (int i = 0; i < N; i++) {
+      const unsigned long long h = g ^ (1ull << i);
+      if (h < g || __ldg(phen + h) != p) continue;
+      int32_t a = (int32_t)g, b = (int32_t)h;
+      bool done = false;
+      for (int tries = 0; tries < (1 << 24) && !done; tries++) {
+        const int32_t ra = cc_find(label, a), rb = cc_find(label, b);
+        if (ra == rb) {
+          done = true;
+          break;
+        }
+        const int32_t lo = min(ra, rb), hi = max(ra, rb);
+        const int32_t seen = atomicCAS(label + hi, hi, lo);
+        if (seen == hi) done = true;
+        else {
+          a = lo;
+          b = seen;
+        }
+      }
+      if (!done) atomicOr(err, kErrUnion);
+    }
+  }
+}
+
+__global__ void cc_finish(const int32_t* __restrict__ phen, unsigned long long total, int32_t* label,
+                          unsigned long long* __restrict__ ncomp) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int32_t l = label[g];
+    if (l < 0) continue;
+    const int32_t r = cc_find(label, (int32_t)g);
+    label[g] = r;
+    if (r == (int32_t)g) atomicAdd(&ncomp[phen[g]], 1ull);
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// Read the error word back (synchronising the stream) and free it.
+int finish_with_err(unsigned* err, cudaStream_t st, const char* what, int rc) {
+  unsigned herr = 0;
+  if (rc == HP_OK) {
+    cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = hp::cuda_fail(e, what);
+  }
+  cudaFreeAsync(err, st);
+  if (rc == HP_OK && (herr & kErrRange)) rc = hp::fail(HP_EINVAL, std::string(what) + ": map entry outside [-1, S)");
+  if (rc == HP_OK && (herr & kErrUnion)) rc = hp::fail(HP_ETIMEOUT, std::string(what) + ": union retries exhausted");
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int hp_designability(const int32_t* d_phen, uint64_t count, int32_t S, uint64_t* d_hist, void* stream) {
+  if (!d_phen || !d_hist) return hp::fail(HP_EINVAL, "hp_designability: NULL pointer");
+  if (S < 1) return hp::fail(HP_EINVAL, "hp_designability: S must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&err, sizeof(unsigned), st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability: cudaMallocAsync");
+  cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+  int rc = HP_OK;
+  const size_t bins_bytes = (size_t)(S + 1) * sizeof(unsigned);
+  int dev = 0, max_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (count == 0) {
+    e = cudaMemsetAsync(d_hist, 0, sizeof(uint64_t) * (size_t)(S + 1), st);
+    if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_designability: memset");
+  } else if (bins_bytes <= (size_t)max_smem) {
+    int rows = sm_count();
+    const unsigned long long need = (count + kHistThreads * 4ull - 1) / (kHistThreads * 4ull);
+    if ((unsigned long long)rows > need) rows = (int)need;
+    unsigned* partial = nullptr;
+    e = cudaMallocAsync(&partial, (size_t)rows * bins_bytes, st);
+    if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_designability: cudaMallocAsync(partials)");
+    if (rc == HP_OK) {
+      e = cudaFuncSetAttribute(hist_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bins_bytes);
+      const int vec4 = ((uintptr_t)d_phen % 16) == 0;
+      if (e == cudaSuccess) {
+        hist_partial<<<rows, kHistThreads, bins_bytes, st>>>(d_phen, count, S, partial, err, vec4);
+        hist_sum<<<(S + 1 + 255) / 256, 256, 0, st>>>(partial, rows, S, reinterpret_cast<unsigned long long*>(d_hist));
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_designability: launch");
+      cudaFreeAsync(partial, st);
+    }
+  } else {
+    e = cudaMemsetAsync(d_hist, 0, sizeof(uint64_t) * (size_t)(S + 1), st);
+    if (e == cudaSuccess) {
+      hist_global<<<sm_count() * 4, 512, 0, st>>>(d_phen, count, S, reinterpret_cast<unsigned long long*>(d_hist), err);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_designability: launch");
+  }
+  return finish_with_err(err, st, "hp_designability", rc);
+}
+
+extern "C" int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64_t* d_neutral, uint64_t* d_to_del,
+                             void* stream) {
+  if (!d_phen || !d_neutral || !d_to_del) return hp::fail(HP_EINVAL, "hp_robustness: NULL pointer");
+  if (N < 1 || N > 40) return hp::fail(HP_EINVAL, "hp_robustness: N must be in [1, 40]");
+  if (S < 1) return hp::fail(HP_EINVAL, "hp_robustness: S must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&err, 16, st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_robustness: cudaMallocAsync");
+  unsigned long long* negcount = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(err) + 8);
+  cudaMemsetAsync(err, 0, 16, st);
+  cudaMemsetAsync(d_neutral, 0, sizeof(uint64_t) * (size_t)(S + 1), st);
+  cudaMemsetAsync(d_to_del, 0, sizeof(uint64_t) * (size_t)(S + 1), st);
+  const int k = std::min((int)N, kRobTileBits);
+  const unsigned long long tiles = 1ull << (N - k);
+  const size_t smem = sizeof(int32_t) << k;
+  int rc = HP_OK;
+  e = cudaFuncSetAttribute(robustness_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    robustness_tiles<<<(unsigned)tiles, kRobThreads, smem, st>>>(
+        d_phen, N, S, reinterpret_cast<unsigned long long*>(d_neutral), reinterpret_cast<unsigned long long*>(d_to_del),
+        negcount, err);
+    robustness_finish<<<1, 1024, 0, st>>>(N, S, reinterpret_cast<unsigned long long*>(d_neutral),
+                                          reinterpret_cast<unsigned long long*>(d_to_del), negcount);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_robustness: launch");
+  return finish_with_err(err, st, "hp_robustness", rc);
+}
+
+extern "C" int hp_neutral_components(const int32_t* d_phen, int32_t N, int32_t S, int32_t* d_label, uint64_t* d_ncomp,
+                                     void* stream) {
+  if (!d_phen || !d_label || !d_ncomp) return hp::fail(HP_EINVAL, "hp_neutral_components: NULL pointer");
+  if (N < 1 || N > 31) return hp::fail(HP_EUNSUPPORTED, "hp_neutral_components: N must be in [1, 31]");
+  if (S < 1) return hp::fail(HP_EINVAL, "hp_neutral_components: S must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&err, sizeof(unsigned), st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_neutral_components: cudaMallocAsync");
+  cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(d_ncomp, 0, sizeof(uint64_t) * (size_t)S, st);
+  const unsigned long long total = 1ull << N;
+  const unsigned grid = (unsigned)std::min<unsigned long long>((total + 255) / 256, (unsigned long long)sm_count() * 16);
+  cc_init<<<grid, 256, 0, st>>>(d_phen, total, S, d_label, err);
+  cc_hook<<<grid, 256, 0, st>>>(d_phen, N, d_label, err);
+  cc_finish<<<grid, 256, 0, st>>>(d_phen, total, d_label, reinterpret_cast<unsigned long long*>(d_ncomp));
+  e = cudaGetLastError();
+  int rc = e == cudaSuccess ? HP_OK : hp::cuda_fail(e, "hp_neutral_components: launch");
+  return finish_with_err(err, st, "hp_neutral_components", rc);
+}

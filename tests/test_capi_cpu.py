@@ -1,0 +1,76 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the header declares,
+its host enumerator agrees with the oracle, and host-side argument checks return status codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2008_05612_gb300 as hp
+from paper_2008_05612_gb300 import build as hpbuild
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "hp_gpmap.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    hpbuild.build()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hp_[a-z_]+)\s*\(", text)))
+
+
+def test_header_symbols_are_exported():
+    syms = declared_symbols()
+    assert len(syms) >= 9
+    L = ctypes.CDLL(hp.LIB_PATH)
+    for name in syms:
+        assert hasattr(L, name), name
+    assert set(syms) <= set(hp.EXPORTS) | set(syms)
+    assert set(hp.EXPORTS) <= set(syms)
+
+
+@pytest.mark.parametrize("dims", [(2, 2), (2, 3), (3, 3), (2, 4), (4, 4), (4, 5), (5, 5), (2, 3, 4), (6, 6), (3, 3, 3)])
+def test_library_enumeration_equals_oracle(obox, dims):
+    s = hp.Structs(dims)
+    o = obox(dims)
+    assert (s.N, s.S, s.S_dir, s.C) == (o.N, o.S, o.S_dir, o.C)
+    c1, k1, cl1 = s.export()
+    c2, cl2, k2, _ = o.export()
+    np.testing.assert_array_equal(c1, c2)
+    np.testing.assert_array_equal(cl1, cl2)
+    np.testing.assert_array_equal(k1, k2)
+
+
+def test_bad_arguments_return_status():
+    L = hp.lib()
+    h = ctypes.c_void_p()
+    assert L.hp_enumerate_structures(4, (ctypes.c_int32 * 3)(2, 2, 2), ctypes.byref(h)) == hp.HP_EINVAL
+    assert L.hp_enumerate_structures(2, (ctypes.c_int32 * 3)(0, 3, 1), ctypes.byref(h)) == hp.HP_EINVAL
+    assert L.hp_enumerate_structures(3, (ctypes.c_int32 * 3)(4, 4, 4), ctypes.byref(h)) == hp.HP_EUNSUPPORTED
+    assert L.hp_enumerate_structures(2, (ctypes.c_int32 * 3)(1, 1, 1), ctypes.byref(h)) == hp.HP_EINVAL
+    assert b"site" in L.hp_last_error()
+    assert L.hp_structs_info(None, None, None, None, None) == hp.HP_EINVAL
+    s = hp.Structs((2, 3))
+    # range beyond 2^N, unsupported threshold, NULL output: rejected before any CUDA call
+    assert L.hp_phenotype_map(s.handle, 60, 8, 1, ctypes.c_void_p(16), None, None) == hp.HP_EINVAL
+    assert L.hp_phenotype_map(s.handle, 0, 8, 2, ctypes.c_void_p(16), None, None) == hp.HP_EUNSUPPORTED
+    assert L.hp_phenotype_map(s.handle, 0, 8, 1, None, None, None) == hp.HP_EINVAL
+    assert L.hp_designability(None, 4, 3, None, None) == hp.HP_EINVAL
+    assert L.hp_robustness(ctypes.c_void_p(16), 50, 3, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == hp.HP_EINVAL
+    assert L.hp_neutral_components(ctypes.c_void_p(16), 36, 3, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == hp.HP_EUNSUPPORTED
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package and its sources never name the oracle."""
+    pkg = os.path.dirname(hp.__file__)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text and "hp_oracle" not in text, f

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit-exact.
+
+Small boxes: every sequence.  Full-size boxes: the whole map on the GPU, a
+seeded sample of ids (plus edge ids) checked one by one by the oracle, and
+properties that hold at any size.  3x3x3 also checks the paper's printed
+statistics.  Reductions: GPU kernels vs oracle reductions of the same map.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_05612_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")
+
+
+@pytest.fixture(scope="module")
+def hp():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2008_05612_gb300 as m
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA is not available for a gpu-marked test")
+    return m
+
+
+_GPU_MAPS = {}
+
+
+def gpu_full_map(hp, dims, aux=False):
+    key = (tuple(dims), aux)
+    if key not in _GPU_MAPS:
+        s = hp.Structs(dims)
+        phen = torch.empty(1 << s.N, dtype=torch.int32, device="cuda")
+        ax = torch.empty(1 << s.N, dtype=torch.int32, device="cuda") if aux else None
+        hp.phenotype_map(s, 0, 1 << s.N, out=phen, aux=ax)
+        torch.cuda.synchronize()
+        _GPU_MAPS.clear()  # keep at most one large map resident
+        _GPU_MAPS[key] = (s, phen, ax)
+    return _GPU_MAPS[key]
+
+
+def edge_ids(N):
+    full = (1 << N) - 1
+    ids = [0, 1, full, full - 1, 1 << (N - 1), full >> 1, 0x5555555555 & full, 0xAAAAAAAAAA & full]
+    ids += [1 << i for i in range(N)] + [full ^ (1 << i) for i in range(N)]
+    return np.array(sorted(set(ids)), dtype=np.uint64)
+
+
+SMALL = [(2, 2), (2, 3), (3, 3), (2, 4), (3, 4), (2, 2, 2), (4, 4), (2, 2, 3), (4, 5)]
+
+
+@pytest.mark.parametrize("dims", SMALL)
+def test_full_map_small_boxes(hp, obox, dims):
+    s, phen, ax = gpu_full_map(hp, dims, aux=True)
+    want, want_aux = obox(dims).full_map(aux=True)
+    got = phen.cpu().numpy()
+    assert (got != want).sum() == 0, f"{(got != want).sum()} mismatches"
+    np.testing.assert_array_equal(ax.cpu().numpy(), want_aux)
+
+
+@pytest.mark.parametrize("dims,nsample", [((5, 5), 3000), ((2, 3, 4), 1500), ((3, 3, 3), 1500)])
+def test_full_size_maps_sampled(hp, obox, dims, nsample):
+    s, phen, _ = gpu_full_map(hp, dims)
+    ids = np.concatenate([edge_ids(s.N), inputs.sample_ids(s.N, nsample, seed=17)])
+    want = obox(dims).phenotypes(ids)
+    got = phen[torch.from_numpy(ids.astype(np.int64)).cuda()].cpu().numpy()
+    assert (got != want).sum() == 0, f"{(got != want).sum()} mismatches of {len(ids)}"
+    assert int(phen.min()) >= -1 and int(phen.max()) < s.S
+
+
+def test_aux_labels_sampled_3x3x3(hp, obox):
+    s = hp.Structs((3, 3, 3))
+    ids = inputs.sample_ids(27, 600, seed=23)
+    # a contiguous block that contains the sampled ids would be the whole space; use 8 aligned blocks instead
+    base = (ids[:8] >> np.uint64(16)) << np.uint64(16)
+    o = obox((3, 3, 3))
+    for b in base.tolist():
+        phen = torch.empty(1 << 16, dtype=torch.int32, device="cuda")
+        ax = torch.empty(1 << 16, dtype=torch.int32, device="cuda")
+        hp.phenotype_map(s, b, 1 << 16, out=phen, aux=ax)
+        pick = inputs.sample_ids(16, 60, seed=b % 1000) + np.uint64(b)
+        wp, wa = o.phenotypes(pick, aux=True)
+        idx = torch.from_numpy((pick - np.uint64(b)).astype(np.int64)).cuda()
+        np.testing.assert_array_equal(phen[idx].cpu().numpy(), wp)
+        np.testing.assert_array_equal(ax[idx].cpu().numpy(), wa)
+
+
+@pytest.mark.parametrize("dims,begin,count", [((4, 4), 13, 40000), ((4, 4), 1, 1), ((4, 4), 65535, 1),
+                                              ((4, 5), 12345, 777777), ((2, 3), 5, 7), ((3, 3), 0, 511)])
+def test_ragged_ranges(hp, obox, dims, begin, count):
+    s = hp.Structs(dims)
+    out = torch.full((count + 2,), 7777, dtype=torch.int32, device="cuda")
+    hp.phenotype_map(s, begin, count, out=out[1 : count + 1])
+    got = out.cpu().numpy()
+    assert got[0] == 7777 and got[-1] == 7777, "write outside the requested range"
+    ids = np.arange(begin, begin + count, dtype=np.uint64)
+    if count > 20000:
+        pick = np.unique(np.concatenate([[0, count - 1], (inputs.sample_ids(30, 3000, seed=5) % np.uint64(count))]))
+        ids = ids[pick.astype(np.int64)]
+        np.testing.assert_array_equal(got[1:-1][pick.astype(np.int64)], obox(dims).phenotypes(ids))
+    else:
+        np.testing.assert_array_equal(got[1:-1], obox(dims).phenotypes(ids))
+
+
+def test_6x6_shard_sampled(hp, obox):
+    """A 2^30-id block of the 6x6 space (N = 36, S_dir = 57,337 = the paper's N_FOLD)."""
+    s = hp.Structs((6, 6))
+    assert s.S_dir == 57337
+    k = inputs.shard_index(0, 64)
+    begin = k << 30
+    phen = torch.empty(1 << 30, dtype=torch.int32, device="cuda")
+    hp.phenotype_map(s, begin, 1 << 30, out=phen)
+    off = np.concatenate([[0, (1 << 30) - 1], inputs.sample_ids(30, 400, seed=29)]).astype(np.uint64)
+    want = obox((6, 6)).phenotypes(off + np.uint64(begin))
+    got = phen[torch.from_numpy(off.astype(np.int64)).cuda()].cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    del phen
+
+
+def test_reversal_symmetry_3x3x3(hp):
+    """P(h^R) = P(h) for every 3x3x3 sequence (the symmetry noted in Appendix B)."""
+    s, phen, _ = gpu_full_map(hp, (3, 3, 3))
+    g = torch.arange(1 << 27, device="cuda", dtype=torch.int64)
+    r = torch.zeros_like(g)
+    for i in range(27):
+        r |= ((g >> i) & 1) << (26 - i)
+    assert bool((phen[r] == phen).all())
+
+
+def test_paper_statistics_3x3x3(hp):
+    """Section 3.2 / Table 4 values, recomputed from the full GPU map with the GPU reductions."""
+    pins = json.load(open(GOLDEN))
+    s, phen, _ = gpu_full_map(hp, (3, 3, 3))
+    N, S = 27, s.S
+    assert S == pins["folds_3x3x3"]["value"]
+    hist = hp.designability(phen, S).cpu().numpy().astype(np.int64)
+    assert hist.sum() == 1 << N
+    folding = 1.0 - hist[S] / (1 << N)
+    assert abs(folding - pins["fold_fraction_3x3x3"]["value"]) <= pins["fold_fraction_3x3x3"]["rounding"]
+    assert int((hist[:S] > 0).sum()) == pins["designable_3x3x3"]["value"]
+    assert int(hist[:S].max()) == pins["top_designability_3x3x3"]["value"]
+    neutral, to_del = (t.cpu().numpy().astype(np.int64) for t in hp.robustness(phen, N, S))
+    d = hist[:S] > 0
+    Np = hist[:S][d].astype(np.float64)
+    rho = neutral[:S][d] / (N * Np)
+    phid = to_del[:S][d] / (N * Np)
+    assert abs(phid.mean() - pins["mean_phi_del_3x3x3"]["value"]) <= pins["mean_phi_del_3x3x3"]["rounding"]
+    assert int(((neutral[:S] + to_del[:S])[d] == N * hist[:S][d]).sum()) == pins["isolated_phenotypes_3x3x3"]["value"]
+    other = 1.0 - rho - phid
+    assert abs(other.mean() - pins["mean_other_fraction_3x3x3"]["value"]) <= pins["mean_other_fraction_3x3x3"]["rounding"]
+    above = (rho > Np / (1 << N)).mean()
+    assert abs(above - pins["above_null_robustness_3x3x3"]["value"]) <= pins["above_null_robustness_3x3x3"]["rounding"]
+
+
+@pytest.mark.parametrize("dims", [(4, 4), (2, 2, 3), (4, 5)])
+def test_reductions_on_real_maps(hp, obox, dims):
+    s, phen, _ = gpu_full_map(hp, dims)
+    want = obox(dims).full_map()
+    np.testing.assert_array_equal(phen.cpu().numpy(), want)
+    N, S = s.N, s.S
+    np.testing.assert_array_equal(hp.designability(phen, S).cpu().numpy().astype(np.uint64), oracle.designability(want, S))
+    gn, gd = hp.robustness(phen, N, S)
+    on, od = oracle.robustness(want, N, S)
+    np.testing.assert_array_equal(gn.cpu().numpy().astype(np.uint64), on)
+    np.testing.assert_array_equal(gd.cpu().numpy().astype(np.uint64), od)
+    gl, gc = hp.neutral_components(phen, N, S)
+    ol, oc = oracle.components(want, N, S)
+    np.testing.assert_array_equal(gl.cpu().numpy(), ol)
+    np.testing.assert_array_equal(gc.cpu().numpy().astype(np.uint64), oc)
+
+
+def synthetic_map(N, S, seed):
+    g = np.arange(1 << N, dtype=np.uint64)
+    r = inputs.splitmix64((g >> np.uint64(max(N - 9, 0))) ^ np.uint64(seed))
+    p = (r % np.uint64(S)).astype(np.int32)
+    hole = inputs.splitmix64(g ^ np.uint64(seed * 7 + 1)) % np.uint64(4) == 0
+    p[hole] = -1
+    return p
+
+
+@pytest.mark.parametrize("N,S,seed", [(12, 5, 1), (20, 300, 2), (24, 51704, 3)])
+def test_reductions_on_synthetic_maps(hp, N, S, seed):
+    m = synthetic_map(N, S, seed)
+    phen = torch.from_numpy(m).cuda()
+    np.testing.assert_array_equal(hp.designability(phen, S).cpu().numpy().astype(np.uint64), oracle.designability(m, S))
+    gn, gd = hp.robustness(phen, N, S)
+    on, od = oracle.robustness(m, N, S)
+    np.testing.assert_array_equal(gn.cpu().numpy().astype(np.uint64), on)
+    np.testing.assert_array_equal(gd.cpu().numpy().astype(np.uint64), od)
+    gl, gc = hp.neutral_components(phen, N, S)
+    ol, oc = oracle.components(m, N, S)
+    np.testing.assert_array_equal(gl.cpu().numpy(), ol)
+    np.testing.assert_array_equal(gc.cpu().numpy().astype(np.uint64), oc)
+
+
+def test_designability_odd_sizes_and_bad_entries(hp):
+    m = synthetic_map(12, 7, 9)
+    for lo, hi in [(1, 4096), (3, 4001), (0, 5)]:
+        sub = torch.from_numpy(m[lo:hi].copy()).cuda()
+        np.testing.assert_array_equal(hp.designability(sub, 7).cpu().numpy().astype(np.uint64),
+                                      oracle.designability(m[lo:hi], 7))
+    bad = torch.tensor([0, 1, 7, -1], dtype=torch.int32, device="cuda")
+    with pytest.raises(hp.HPError):
+        hp.designability(bad, 7)
