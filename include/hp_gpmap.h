@@ -91,6 +91,23 @@ int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_t seq_count
  *   next synchronising call of this library (they are counted nowhere). */
 int hp_designability(const int32_t* d_phen, uint64_t count, int32_t S, uint64_t* d_hist, void* stream);
 
+/* Designability without any device allocation: the same result as
+ * hp_designability, for callers that must not have a library allocate device
+ * memory -- typically a process whose framework or service already owns the
+ * device memory in its own pool, where cudaMalloc/cudaMallocAsync could fail or
+ * fragment that pool, or code held to a fixed device-memory budget.  The paper
+ * has no counterpart; this is an interface convenience of this library.
+ *   Scratch (partial histograms and the error word) is a 4 MiB file-scope
+ *   device array that every GPU loading the library holds until exit.
+ *   Limit: S + 1 bins must fit one shared-memory histogram and the scratch
+ *   (S + 1 <= 58,112 on GB300); larger S returns HP_EINVAL with the limit.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the array: calls that overlap on the GPU (other streams,
+ *   other host threads) race and must be serialised by the caller.
+ *   Synchronises `stream` before returning (it reads the error word back). */
+int hp_designability_noalloc(const int32_t* d_phen, uint64_t count, int32_t S, uint64_t* d_hist, void* stream);
+
 /* Numerators of Eq. 2 for p = q, over a FULL map of 2^N sequences (K = 2, so
  * every genotype has (K-1)L = N single-flip neighbours):
  *   d_neutral[p] = sum over g with P(g) = p of #{i : P(g xor 2^i) = p}

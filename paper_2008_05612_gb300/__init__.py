@@ -23,7 +23,8 @@ _STATUS = {0: "HP_OK", -1: "HP_EINVAL", -2: "HP_ENOMEM", -3: "HP_ECUDA", -4: "HP
 # every symbol the header declares (checked by the CPU test-suite)
 EXPORTS = (
     "hp_enumerate_structures", "hp_structs_info", "hp_structs_export", "hp_structs_free",
-    "hp_phenotype_map", "hp_designability", "hp_robustness", "hp_neutral_components", "hp_last_error",
+    "hp_phenotype_map", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
+    "hp_last_error",
 )
 
 _lib = None
@@ -53,6 +54,7 @@ def lib():
         L.hp_structs_free.restype = None
         L.hp_phenotype_map.argtypes = [vp, u64, u64, i32, vp, vp, vp]
         L.hp_designability.argtypes = [vp, u64, i32, vp, vp]
+        L.hp_designability_noalloc.argtypes = [vp, u64, i32, vp, vp]
         L.hp_robustness.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_neutral_components.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_last_error.restype = ctypes.c_char_p
@@ -147,6 +149,16 @@ def designability(phen, S: int, out=None, stream=None):
         out = torch.empty(S + 1, dtype=torch.int64, device=phen.device)
     _check(lib().hp_designability(_dptr(phen, torch.int32, "phen"), phen.numel(), S, _dptr(out, torch.int64, "out"),
                                   _stream_ptr(stream)))
+    return out
+
+
+def designability_noalloc(phen, S: int, out, stream=None):
+    """hp_designability_noalloc: designability into a caller-provided int64[S+1] tensor, with no device
+    allocation by the library (scratch is a static device array shared by all calls)."""
+    import torch
+
+    _check(lib().hp_designability_noalloc(_dptr(phen, torch.int32, "phen"), phen.numel(), S,
+                                          _dptr(out, torch.int64, "out"), _stream_ptr(stream)))
     return out
 
 

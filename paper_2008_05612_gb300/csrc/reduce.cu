@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "hp_internal.h"
@@ -331,4 +332,92 @@ extern "C" int hp_neutral_components(const int32_t* d_phen, int32_t N, int32_t S
   e = cudaGetLastError();
   int rc = e == cudaSuccess ? HP_OK : hp::cuda_fail(e, "hp_neutral_components: launch");
   return finish_with_err(err, st, "hp_neutral_components", rc);
+}
+
+// ---------------------------------------------------------------- designability without allocation
+//
+// Some callers cannot let a library allocate device memory: a process whose
+// framework or service has already reserved the device's memory in its own
+// pool (where cudaMalloc / cudaMallocAsync would fail or fragment that pool),
+// or code with a fixed device-memory budget.  For them the partial histograms
+// and the error word of the designability pass live in one file-scope device
+// array instead of per-call allocations.  Host code may not pass the array's
+// name to a kernel (that is a host-side stand-in, not a device address): its
+// device address is looked up once per device with cudaGetSymbolAddress.
+
+namespace {
+
+constexpr size_t kNoAllocWords = 1u << 20;  // 4 MiB of scratch, held by every GPU that loads the library
+constexpr size_t kNoAllocHeader = 64;       // word 0: error word; partial rows start 256 bytes in
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned g_noalloc_scratch[kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+unsigned* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (set up on first use).
+int noalloc_scratch(unsigned** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return hp::fail(HP_EUNSUPPORTED, "hp_designability_noalloc: device index too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = static_cast<unsigned*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return HP_OK;
+}
+
+}  // namespace
+
+extern "C" int hp_designability_noalloc(const int32_t* d_phen, uint64_t count, int32_t S, uint64_t* d_hist,
+                                        void* stream) {
+  if (!d_phen || !d_hist) return hp::fail(HP_EINVAL, "hp_designability_noalloc: NULL pointer");
+  if (S < 1) return hp::fail(HP_EINVAL, "hp_designability_noalloc: S must be >= 1");
+  int dev = 0, max_smem = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: cudaGetDevice");
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t bins = (size_t)S + 1;
+  const size_t bins_bytes = bins * sizeof(unsigned);
+  if (bins_bytes > (size_t)max_smem || bins > kNoAllocWords - kNoAllocHeader)
+    return hp::fail(HP_EINVAL, "hp_designability_noalloc: S + 1 = " + std::to_string(bins) +
+                                   " bins exceed the limit of this entry point (" +
+                                   std::to_string(std::min((size_t)max_smem / sizeof(unsigned), kNoAllocWords - kNoAllocHeader)) +
+                                   " bins: one shared-memory histogram and the 4 MiB static scratch)");
+  unsigned* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != HP_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* err = scratch;
+  unsigned* partial = scratch + kNoAllocHeader;
+  int rows = (int)std::min<size_t>((size_t)sm_count(), (kNoAllocWords - kNoAllocHeader) / bins);
+  const unsigned long long need = (count + kHistThreads * 4ull - 1) / (kHistThreads * 4ull);
+  if ((unsigned long long)rows > need) rows = (int)std::max<unsigned long long>(need, 1ull);
+  // the error word starts at zero; every partial row is fully overwritten by its CTA
+  e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: cudaMemsetAsync");
+  if (count == 0) {
+    e = cudaMemsetAsync(d_hist, 0, sizeof(uint64_t) * bins, st);
+  } else {
+    e = cudaFuncSetAttribute(hist_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bins_bytes);
+    if (e == cudaSuccess) {
+      const int vec4 = ((uintptr_t)d_phen % 16) == 0;
+      hist_partial<<<rows, kHistThreads, bins_bytes, st>>>(d_phen, count, S, partial, err, vec4);
+      hist_sum<<<(unsigned)((bins + 255) / 256), 256, 0, st>>>(partial, rows, S, reinterpret_cast<unsigned long long*>(d_hist));
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: launch");
+  unsigned herr = 0;
+  e = cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: execution");
+  if (herr & kErrRange) return hp::fail(HP_EINVAL, "hp_designability_noalloc: map entry outside [-1, S)");
+  return HP_OK;
 }
