@@ -155,6 +155,36 @@ def run_reference(args):
     return 0
 
 
+def run_map_only(args):
+    """Phenotype map of one aligned id block, W + K launches, CUDA-event timed (a small case for ncu)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2008_05612_gb300 as hp
+
+    box, bits = args.map_only.split(":")
+    dims = tuple(int(x) for x in box.split("x"))
+    bits = int(bits)
+    s = hp.Structs(dims)
+    n = 1 << bits
+    phen = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        hp.phenotype_map(s, 0, n, out=phen)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        hp.phenotype_map(s, 0, n, out=phen)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": args.map_only, "ms_per_launch": ms, "evals_per_s": n * s.S_dir / (ms * 1e-3),
+                      "sequences": n, "conformations": s.S_dir}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -162,9 +192,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--map-only", default=None, metavar="BOX:BITS",
+                    help="profiling case: only the phenotype map of ids [0, 2^BITS) of BOX (e.g. 6x6:27)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.map_only:
+        return run_map_only(args)
 
     import torch
 

@@ -84,6 +84,56 @@ void hp_structs_free(hp_structs* s);
 int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_t seq_count, int32_t gap_threshold,
                      int32_t* d_phen, int32_t* d_argmin_aux, void* stream);
 
+/* Kernel shape of the phenotype map: 2^reg_bits sequences per thread (32 =
+ * one 32-bit word of sequences per lane at reg_bits 5) and `tile`
+ * conformations per shared-memory tile.  Compiled shapes: reg_bits 4 with tile
+ * 64 or 128; reg_bits 5 or 6 with tile 64, 128 or 256.  Results never depend
+ * on the shape, only speed does.  (No counterpart in the paper, whose kernel
+ * had one thread per sequence; Figure 4 sweeps its launch shape instead.) */
+typedef struct {
+  int32_t reg_bits;
+  int32_t tile;
+} hp_tile_cfg;
+
+/* Shape used by hp_phenotype_map for this library; NULL restores the default
+ * (reg_bits 5, tile 256).  HP_EINVAL for a shape that is not compiled. */
+int hp_set_tile_cfg(hp_structs* s, const hp_tile_cfg* cfg);
+int hp_get_tile_cfg(const hp_structs* s, hp_tile_cfg* cfg);
+/* The compiled shapes: writes up to *n entries to cfgs (may be NULL) and sets
+ * *n to the number of shapes. */
+int hp_tile_cfg_list(hp_tile_cfg* cfgs, int32_t* n);
+
+/* Autotuner (the analogue of the paper's launch-shape sweep, Section 2.2,
+ * Figure 4): times every compiled shape on two waves of work items of this
+ * box on the current device, keeps the fastest on the library (as by
+ * hp_set_tile_cfg) and returns it in *best (may be NULL).  ms (may be NULL)
+ * receives one time per shape in hp_tile_cfg_list order (-1: does not fit).
+ * Allocates a stream-ordered scratch map of up to 2^28 ids; synchronises. */
+int hp_autotune(hp_structs* s, hp_tile_cfg* best, float* ms, void* stream);
+
+/* Batched persistent launch: the phenotype maps of n boxes (1 <= n <= 8, any
+ * shapes and sizes) and their id ranges in ONE launch of the phenotype kernel,
+ * whose CTAs take work items from a shared queue (boxes with more
+ * conformations first).  Entry i computes exactly what
+ * hp_phenotype_map(libs[i], begins[i], counts[i], 1, d_phen[i], NULL) would.
+ *   cfg: kernel shape for the launch, NULL for libs[0]'s (see hp_set_tile_cfg).
+ * Synchronises `stream` before returning (it reads the error word back). */
+int hp_phenotype_map_batch(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int32_t n,
+                           int32_t* const* d_phen, const hp_tile_cfg* cfg, void* stream);
+
+/* A batch captured once into a CUDA graph (queue reset + persistent launch).
+ * Create uploads the tables and captures on a private stream; launch replays
+ * the graph on `stream` without synchronising; status synchronises `stream`
+ * and reports a device-side timeout of the replays since the last status.
+ * The plan keeps the library handles and output pointers it was made with:
+ * they must outlive it.  Plans must not be launched concurrently. */
+typedef struct hp_batch_plan hp_batch_plan;
+int hp_batch_plan_create(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int32_t n,
+                         int32_t* const* d_phen, const hp_tile_cfg* cfg, void* stream, hp_batch_plan** out);
+int hp_batch_plan_launch(hp_batch_plan* plan, void* stream);
+int hp_batch_plan_status(hp_batch_plan* plan, void* stream);
+void hp_batch_plan_free(hp_batch_plan* plan);
+
 /* Designability (Section 2.3): d_hist[p] = #{k : d_phen[k] = p} for
  * p in [0, S), d_hist[S] = #{k : d_phen[k] = -1}.
  *   d_phen: device int32[count], entries in [-1, S); d_hist: device

@@ -23,9 +23,19 @@ _STATUS = {0: "HP_OK", -1: "HP_EINVAL", -2: "HP_ENOMEM", -3: "HP_ECUDA", -4: "HP
 # every symbol the header declares (checked by the CPU test-suite)
 EXPORTS = (
     "hp_enumerate_structures", "hp_structs_info", "hp_structs_export", "hp_structs_free",
-    "hp_phenotype_map", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
+    "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
+    "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
+    "hp_batch_plan_free", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
     "hp_last_error",
 )
+_VOID = ("hp_structs_free", "hp_last_error", "hp_batch_plan_free")
+
+
+class TileCfg(ctypes.Structure):
+    _fields_ = [("reg_bits", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+    def __repr__(self):
+        return f"TileCfg(reg_bits={self.reg_bits}, tile={self.tile})"
 
 _lib = None
 _lock = threading.Lock()
@@ -53,13 +63,23 @@ def lib():
         L.hp_structs_free.argtypes = [vp]
         L.hp_structs_free.restype = None
         L.hp_phenotype_map.argtypes = [vp, u64, u64, i32, vp, vp, vp]
+        L.hp_set_tile_cfg.argtypes = [vp, vp]
+        L.hp_get_tile_cfg.argtypes = [vp, vp]
+        L.hp_tile_cfg_list.argtypes = [vp, vp]
+        L.hp_autotune.argtypes = [vp, vp, vp, vp]
+        L.hp_phenotype_map_batch.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.hp_batch_plan_create.argtypes = [vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
+        L.hp_batch_plan_launch.argtypes = [vp, vp]
+        L.hp_batch_plan_status.argtypes = [vp, vp]
+        L.hp_batch_plan_free.argtypes = [vp]
+        L.hp_batch_plan_free.restype = None
         L.hp_designability.argtypes = [vp, u64, i32, vp, vp]
         L.hp_designability_noalloc.argtypes = [vp, u64, i32, vp, vp]
         L.hp_robustness.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_neutral_components.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name != "hp_structs_free" and name != "hp_last_error":
+            if name not in _VOID:
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -113,6 +133,27 @@ class Structs:
             _lib.hp_structs_free(h)
             self._h = None
 
+    def set_tile_cfg(self, reg_bits=None, tile=None):
+        """hp_set_tile_cfg; no arguments restores the default shape."""
+        if reg_bits is None:
+            _check(lib().hp_set_tile_cfg(self._h, None))
+        else:
+            c = TileCfg(reg_bits, tile)
+            _check(lib().hp_set_tile_cfg(self._h, ctypes.byref(c)))
+
+    def tile_cfg(self):
+        c = TileCfg()
+        _check(lib().hp_get_tile_cfg(self._h, ctypes.byref(c)))
+        return (c.reg_bits, c.tile)
+
+    def autotune(self, stream=None):
+        """hp_autotune: returns (best (reg_bits, tile), {shape: ms})."""
+        shapes = tile_cfg_list()
+        ms = (ctypes.c_float * len(shapes))()
+        best = TileCfg()
+        _check(lib().hp_autotune(self._h, ctypes.byref(best), ms, _stream_ptr(stream)))
+        return (best.reg_bits, best.tile), {sh: float(ms[i]) for i, sh in enumerate(shapes)}
+
     def export(self):
         """(coords S_dir x N uint8, contacts S_dir x C x 2 uint8, conf_class S_dir int32)"""
         coords = np.zeros((self.S_dir, self.N), dtype=np.uint8)
@@ -140,6 +181,62 @@ def phenotype_map(structs: Structs, begin: int = 0, count: int | None = None, ou
     _check(lib().hp_phenotype_map(structs.handle, begin, count, gap_threshold, _dptr(out, torch.int32, "out"), paux,
                                   _stream_ptr(stream)))
     return out
+
+
+def tile_cfg_list():
+    """Compiled kernel shapes (reg_bits, tile) (hp_tile_cfg_list)."""
+    n = ctypes.c_int32(0)
+    _check(lib().hp_tile_cfg_list(None, ctypes.byref(n)))
+    arr = (TileCfg * n.value)()
+    _check(lib().hp_tile_cfg_list(arr, ctypes.byref(n)))
+    return [(c.reg_bits, c.tile) for c in arr]
+
+
+def _batch_args(structs, ranges, outs, cfg):
+    import torch
+
+    n = len(structs)
+    if not (len(ranges) == len(outs) == n):
+        raise ValueError("structs, ranges and outs must have the same length")
+    libs = (ctypes.c_void_p * n)(*[s.handle.value for s in structs])
+    begins = (ctypes.c_uint64 * n)(*[int(r[0]) for r in ranges])
+    counts = (ctypes.c_uint64 * n)(*[int(r[1]) for r in ranges])
+    for o, r in zip(outs, ranges):
+        if o.numel() < int(r[1]):
+            raise ValueError("an output is smaller than its range")
+    ptrs = (ctypes.c_void_p * n)(*[_dptr(o, torch.int32, "out").value for o in outs])
+    c = ctypes.byref(TileCfg(*cfg)) if cfg is not None else None
+    return libs, begins, counts, n, ptrs, c
+
+
+def phenotype_map_batch(structs, ranges, outs, cfg=None, stream=None):
+    """One persistent launch for several boxes (hp_phenotype_map_batch); ranges = [(begin, count)]."""
+    libs, begins, counts, n, ptrs, c = _batch_args(structs, ranges, outs, cfg)
+    _check(lib().hp_phenotype_map_batch(libs, begins, counts, n, ptrs, c, _stream_ptr(stream)))
+    return outs
+
+
+class BatchPlan:
+    """A batch captured into a CUDA graph (hp_batch_plan_*); keeps its inputs alive."""
+
+    def __init__(self, structs, ranges, outs, cfg=None, stream=None):
+        self._keep = (list(structs), list(outs))
+        libs, begins, counts, n, ptrs, c = _batch_args(structs, ranges, outs, cfg)
+        h = ctypes.c_void_p()
+        _check(lib().hp_batch_plan_create(libs, begins, counts, n, ptrs, c, _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().hp_batch_plan_launch(self._h, _stream_ptr(stream)))
+
+    def status(self, stream=None):
+        _check(lib().hp_batch_plan_status(self._h, _stream_ptr(stream)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.hp_batch_plan_free(h)
+            self._h = None
 
 
 def designability(phen, S: int, out=None, stream=None):

@@ -50,6 +50,8 @@ struct hp_structs {
   //   rest     zero padding
   int rec_words = 0;
   std::vector<uint32_t> rec;        // S_dir x rec_words
+  int tile_reg_bits = 0;            // preferred kernel shape (0: library default), see hp_set_tile_cfg
+  int tile_size = 0;
   std::mutex mu;
   std::vector<hp::DevTables*> dev;  // lazily uploaded, one entry per device
 };

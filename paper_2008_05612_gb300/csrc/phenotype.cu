@@ -15,61 +15,46 @@
 // 2^14 even patterns; the coefficients of each conformation are computed once
 // per CTA and the scores of all even patterns are subset sums of them.
 //
-// Layout of the even-pattern bits ("roles"), R = register bits (template):
-//   role 0          split: low/high 16-bit half of a packed register
-//   roles 1..R-1    tree: index of one of the 2^(R-1) packed registers
-//   roles R..R+4    lane of the warp
-//   roles R+5..R+7  warp of the CTA (8 warps)
+// Layout of the 14 even-pattern bits ("roles") for a shape with R register bits:
+//   role 0            split: low/high 16-bit half of a packed register
+//   roles 1..R-1      tree: index of one of the 2^(R-1) packed registers
+//   roles R..R+4      lane of the warp
+//   roles R+5..13     warp of the CTA (2^(9-R) warps)
 // Each thread keeps, per packed register, the running maximum of the doubled,
-// biased score 2 (x + 1) of two sequences (max.u16x2).  Per tile of T
-// conformations the tile maximum is merged into a best value with a tie bit
-// and the tile index where the best was first reached.  A sequence whose best
-// is reached in two tiles is not unique; the others re-scan that one tile in
-// the epilogue (a warp-cooperative exact count with ballots), which also finds
-// the lowest-index conformation at the minimum.
+// biased score 2 (x + 1) of two sequences (max.u16x2; the last tree level uses
+// the fused add + max).  Per tile of T conformations the tile maximum is merged
+// into a best value with a tie bit and the index of the first tile reaching it.
+// A sequence whose best is reached in two tiles is not unique.  Pass 2 stages
+// the tiles again and resolves every other sequence exactly inside its one tile
+// (warp-cooperative count and first index with ballots), which also yields the
+// lowest-index conformation at the minimum.
 //
 // Data movement.  Conformation records (contact masks, see hp_internal.h) are
 // staged tile by tile into shared memory with the bulk-copy engine
 // (cp.async.bulk + mbarrier, bounded waits), double buffered; one thread per
 // conformation turns a record into the CTA's coefficient record (lane table,
-// warp table, packed tree coefficients) in a second double buffer.
+// warp table, packed tree coefficients) in a second double buffer.  CTAs are
+// persistent and take work items (instance, id block, odd pattern, even chunk)
+// from a device counter, so boxes of different shapes share one launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
 
 #include "hp_internal.h"
+#include "phenotype.h"
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kLaneRoles = 5;
-constexpr int kWarpRoles = 3;
-constexpr int kCStride = 52;      // words per coefficient record (13 x 16 B, odd in 16-B units)
-constexpr int kMaxBlocks = 96;    // aligned id blocks per launch
+constexpr int kRoles = 14;  // even-pattern bits covered by one CTA
 constexpr unsigned kErrTimeout = 1u;
 constexpr long long kSpinLimit = 1ll << 26;
-
-struct BlockDesc {
-  unsigned long long g_base;      // first sequence id of the block (aligned to 2^m)
-  unsigned long long out_off;     // index of g_base in the output
-  unsigned long long item_begin;  // first work item of the block
-  unsigned int ne_free, no_free;  // even / odd residues below bit m
-  unsigned int nroles;            // real roles: min(ne_free, R + 8)
-  unsigned int pad;
-};
-
-struct Params {
-  const uint32_t* rec;  // conformation records, padded to a multiple of T
-  const int32_t* conf_class;
-  int32_t* phen;
-  int32_t* aux;
-  unsigned int* err;
-  int S_dir, ntiles, rec_words, NE, NO;
-  int nblocks;
-  unsigned long long total_items;
-  BlockDesc blocks[kMaxBlocks];
-};
 
 __device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
   uint32_t d;
@@ -77,9 +62,7 @@ __device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
   return d;
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
@@ -87,13 +70,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
 }
 
 // Wait for phase `parity` of the barrier; false after kSpinLimit polls.
@@ -132,38 +113,138 @@ __device__ __forceinline__ unsigned long long interleave(uint32_t e, uint32_t o)
 }
 
 // coefficient of even residue 2k for odd pattern o: 10 c_{2k} + 3 #H partners
-__device__ __forceinline__ uint32_t coef(uint32_t mask, uint32_t o) {
-  return 10u * __popc(mask) + 3u * __popc(mask & o);
-}
+__device__ __forceinline__ uint32_t coef(uint32_t mask, uint32_t o) { return 10u * __popc(mask) + 3u * __popc(mask & o); }
 // score part that depends on the odd residues only: 10 sum_j o_j c_j
 __device__ __forceinline__ uint32_t odd_part(const uint32_t* r, int NE, uint32_t o) {
   return 10u * (__popc(o & r[NE]) + 2u * __popc(o & r[NE + 1]) + 4u * __popc(o & r[NE + 2]));
 }
 
-template <int R, int T>
-struct Smem {
+// Compile-time shape: R register bits (2^(R-1) packed registers of two
+// sequences per thread), T conformations per shared-memory tile, 2^(9-R) warps.
+template <int R_, int T_>
+struct Cfg {
+  static constexpr int R = R_, T = T_, WB = kRoles - kLaneRoles - R_;
   static constexpr int P = 1 << (R - 1);
-  static constexpr int kCoefWords = 2 * T * kCStride;
-  static constexpr int kStateWords = 2 * P * kThreads;
+  static constexpr int NW = 1 << WB;
+  static constexpr int THREADS = 32 * NW;
+  // coefficient record: lane table [32], warp table [NW], tree coefficients [R-1]
+  static constexpr int WT_OFF = 32;
+  static constexpr int TP_OFF = 32 + NW;
+  static constexpr int TP_WORDS = ((R - 1) + 3) / 4 * 4;
+  static constexpr int CS_RAW = TP_OFF + TP_WORDS;
+  // words per record: a multiple of 4 that is odd in 16-byte units (conflict-free 16-byte stores)
+  static constexpr int CSTRIDE = ((CS_RAW / 4) % 2 == 1) ? CS_RAW : CS_RAW + 4;
+  static constexpr int kCoefWords = 2 * T * CSTRIDE;
+  static constexpr int kStateWords = 2 * P * THREADS;
+  static_assert(T <= THREADS, "one producer thread per conformation of a tile");
+  static_assert(T % 32 == 0 && hp::kRecPad % T == 0, "tiles are whole warps and tile the padded table");
+  static_assert(NW >= 4, "warp tables are written in groups of four");
 };
 
-template <int R, int T>
-__global__ void __launch_bounds__(kThreads, 1) phenotype_kernel(const __grid_constant__ Params p) {
-  constexpr int P = 1 << (R - 1);
-  constexpr int NROLE = R + kLaneRoles + kWarpRoles;
+// Stage tile t's records (bulk copy issued two tiles ahead) and turn them into
+// this CTA's coefficient records: one thread per conformation.  Ends with a
+// CTA barrier; returns false if a bounded wait gave up.
+template <class K>
+__device__ __forceinline__ bool produce_tile(const hp::PhenInst& in, unsigned* err, int t, uint32_t* rawbuf,
+                                             uint32_t* coefbuf, uint64_t* bars, unsigned (&issued)[2],
+                                             unsigned (&waited)[2], uint32_t o, uint32_t ehigh, int nroles,
+                                             int* s_abort) {
+  constexpr int R = K::R, T = K::T;
+  const int tid = threadIdx.x;
+  const int buf = t & 1;
+  const unsigned raw_bytes = (unsigned)(T * in.rec_words * 4);
+  uint32_t* cbuf = coefbuf + buf * T * K::CSTRIDE;
+  if (tid < T) {
+    if (!mbar_wait(&bars[buf], waited[buf] & 1u)) {
+      atomicOr(err, kErrTimeout);
+      *s_abort = 1;
+    } else {
+      const uint32_t* r = rawbuf + buf * T * in.rec_words + tid * in.rec_words;
+      uint32_t* c = cbuf + tid * K::CSTRIDE;
+      const int s = t * T + tid;
+      if (s < in.S_dir) {
+        uint32_t a[kRoles];
+#pragma unroll
+        for (int k = 0; k < kRoles; k++) a[k] = k < nroles ? 2u * coef(r[k], o) : 0u;
+        uint32_t extra = 0;
+        for (int k = nroles; k < in.NE; k++)
+          if ((ehigh >> k) & 1u) extra += coef(r[k], o);
+        const uint32_t base = 2u * (odd_part(r, in.NE, o) + extra + 1u);
+        const uint32_t split_hi = a[0] << 16;
+        // lane table: base + subset sums of the 5 lane coefficients, packed
+        uint32_t lt[32];
+        lt[0] = base;
+#pragma unroll
+        for (int l = 1; l < 32; l++) {
+          const int hb = 31 - __clz(l);
+          lt[l] = lt[l ^ (1 << hb)] + a[R + hb];
+        }
+#pragma unroll
+        for (int l = 0; l < 32; l += 4)
+          *reinterpret_cast<uint4*>(c + l) = make_uint4(lt[l] * 0x10001u + split_hi, lt[l + 1] * 0x10001u + split_hi,
+                                                        lt[l + 2] * 0x10001u + split_hi, lt[l + 3] * 0x10001u + split_hi);
+        uint32_t wt[K::NW];
+        wt[0] = 0;
+#pragma unroll
+        for (int w = 1; w < K::NW; w++) {
+          const int hb = 31 - __clz(w);
+          wt[w] = wt[w ^ (1 << hb)] + a[R + kLaneRoles + hb];
+        }
+#pragma unroll
+        for (int w = 0; w < K::NW; w += 4)
+          *reinterpret_cast<uint4*>(c + K::WT_OFF + w) =
+              make_uint4(wt[w] * 0x10001u, wt[w + 1] * 0x10001u, wt[w + 2] * 0x10001u, wt[w + 3] * 0x10001u);
+        uint32_t tp[K::TP_WORDS];
+#pragma unroll
+        for (int j = 0; j < K::TP_WORDS; j++) tp[j] = j < R - 1 ? a[1 + j] * 0x10001u : 0u;
+#pragma unroll
+        for (int j = 0; j < K::TP_WORDS; j += 4)
+          *reinterpret_cast<uint4*>(c + K::TP_OFF + j) = make_uint4(tp[j], tp[j + 1], tp[j + 2], tp[j + 3]);
+      } else {
+        // padding conformation: every score 0, below every real (biased) score
+#pragma unroll
+        for (int k = 0; k < K::CS_RAW; k += 4) *reinterpret_cast<uint4*>(c + k) = make_uint4(0, 0, 0, 0);
+      }
+    }
+  }
+  waited[buf]++;
+  __syncthreads();
+  if (*s_abort) return false;
+  // raw[buf] has been read by every producer: prefetch tile t + 2 into it
+  if (t + 2 < in.ntiles) {
+    if (tid == 0)
+      bulk_load(rawbuf + buf * T * in.rec_words, in.rec + (size_t)(t + 2) * T * in.rec_words, raw_bytes, &bars[buf]);
+    issued[buf]++;
+  }
+  return true;
+}
+
+template <int T>
+__device__ __forceinline__ void prefetch_first_tiles(const hp::PhenInst& in, uint32_t* rawbuf, uint64_t* bars,
+                                                     unsigned (&issued)[2]) {
+  const unsigned raw_bytes = (unsigned)(T * in.rec_words * 4);
+  if (threadIdx.x == 0) bulk_load(rawbuf, in.rec, raw_bytes, &bars[0]);
+  issued[0]++;
+  if (in.ntiles > 1) {
+    if (threadIdx.x == 0) bulk_load(rawbuf + T * in.rec_words, in.rec + (size_t)T * in.rec_words, raw_bytes, &bars[1]);
+    issued[1]++;
+  }
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_constant__ hp::PhenParams p) {
+  constexpr int R = K::R, T = K::T, P = K::P, kThreads = K::THREADS, CSTRIDE = K::CSTRIDE;
   extern __shared__ __align__(128) uint32_t smem[];
-  // layout: [coef 2 x T x kCStride][raw 2 x T x rec_words] ... [2 mbarriers]; the
-  // epilogue reuses the front as per-thread state (2 x P x kThreads words)
+  // layout: [coef 2 x T x CSTRIDE][raw 2 x T x max_rec_words][state 2 x P x THREADS][2 mbarriers]
   uint32_t* coefbuf = smem;
-  const int coef_words = Smem<R, T>::kCoefWords;
-  const int state_words = Smem<R, T>::kStateWords;
-  const int front = coef_words + 2 * T * p.rec_words;
-  uint32_t* rawbuf = smem + coef_words;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + ((max(front, state_words) + 3) & ~3));
+  uint32_t* rawbuf = smem + K::kCoefWords;
+  uint32_t* st_best = rawbuf + 2 * T * p.max_rec_words;  // [P][THREADS] packed best (doubled score | tie)
+  uint32_t* st_tile = st_best + P * kThreads;             // [P][THREADS] packed tile of the best, then result
+  uint64_t* bars = reinterpret_cast<uint64_t*>(st_tile + P * kThreads);
   __shared__ int s_abort;
+  __shared__ unsigned long long s_item;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned raw_bytes = (unsigned)(T * p.rec_words * 4);
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -173,117 +254,59 @@ __global__ void __launch_bounds__(kThreads, 1) phenotype_kernel(const __grid_con
   __syncthreads();
   // per raw buffer: bulk copies issued and waited for (identical in every thread)
   unsigned issued[2] = {0u, 0u}, waited[2] = {0u, 0u};
+  const uint32_t role_hi = ((uint32_t)lane << R) | ((uint32_t)warp << (R + kLaneRoles));
 
-  for (unsigned long long item = blockIdx.x; item < p.total_items; item += gridDim.x) {
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(reinterpret_cast<unsigned long long*>(p.ctrl + 2), 1ull);
+    __syncthreads();
+    const unsigned long long item = s_item;
+    __syncthreads();  // s_item is rewritten by the next iteration
+    if (item >= p.total_items) break;
     int b = 0;
     while (b + 1 < p.nblocks && p.blocks[b + 1].item_begin <= item) b++;
-    const BlockDesc& bd = p.blocks[b];
+    const hp::PhenBlock& bd = p.blocks[b];
+    const hp::PhenInst& in = p.inst[bd.inst];
     const unsigned long long local = item - bd.item_begin;
     const uint32_t o = odd_bits(bd.g_base) | (uint32_t)(local & ((1ull << bd.no_free) - 1));
     const uint32_t chunk = (uint32_t)(local >> bd.no_free);
     const int nroles = (int)bd.nroles;
     const uint32_t ehigh = even_bits(bd.g_base) | (chunk << nroles);
+    const uint32_t role_mask = (1u << nroles) - 1u;
+    const bool want_aux = in.aux != nullptr;
 
+    // ================= pass 1: running maxima over every conformation
     uint32_t tmax[P], m1[P], ts[P];
 #pragma unroll
     for (int v = 0; v < P; v++) tmax[v] = m1[v] = ts[v] = 0u;
-
-    if (tid == 0) bulk_load(rawbuf, p.rec, raw_bytes, &bars[0]);
-    issued[0]++;
-    if (p.ntiles > 1) {
-      if (tid == 0) bulk_load(rawbuf + T * p.rec_words, p.rec + (size_t)T * p.rec_words, raw_bytes, &bars[1]);
-      issued[1]++;
-    }
-
-    for (int t = 0; t < p.ntiles; t++) {
-      const int buf = t & 1;
-      uint32_t* cbuf = coefbuf + buf * T * kCStride;
-      // ---- producer: one thread per conformation of the tile
-      if (tid < T) {
-        if (!mbar_wait(&bars[buf], waited[buf] & 1u)) {
-          atomicOr(p.err, kErrTimeout);
-          s_abort = 1;
-        } else {
-          const uint32_t* r = rawbuf + buf * T * p.rec_words + tid * p.rec_words;
-          uint32_t* c = cbuf + tid * kCStride;
-          const int s = t * T + tid;
-          if (s < p.S_dir) {
-            uint32_t a[NROLE];
-#pragma unroll
-            for (int k = 0; k < NROLE; k++) a[k] = k < nroles ? 2u * coef(r[k], o) : 0u;
-            uint32_t extra = 0;
-            for (int k = nroles; k < p.NE; k++)
-              if ((ehigh >> k) & 1u) extra += coef(r[k], o);
-            const uint32_t base = 2u * (odd_part(r, p.NE, o) + extra + 1u);
-            const uint32_t split_hi = a[0] << 16;
-            // lane table: base + subset sums of the 5 lane coefficients, packed
-            uint32_t lt[32];
-            lt[0] = base;
-#pragma unroll
-            for (int l = 1; l < 32; l++) {
-              const int hb = 31 - __clz(l);
-              lt[l] = lt[l ^ (1 << hb)] + a[R + hb];
-            }
-#pragma unroll
-            for (int l = 0; l < 32; l += 4)
-              *reinterpret_cast<uint4*>(c + l) = make_uint4(lt[l] * 0x10001u + split_hi, lt[l + 1] * 0x10001u + split_hi,
-                                                            lt[l + 2] * 0x10001u + split_hi, lt[l + 3] * 0x10001u + split_hi);
-            uint32_t wt[8];
-            wt[0] = 0;
-#pragma unroll
-            for (int w = 1; w < 8; w++) {
-              const int hb = 31 - __clz(w);
-              wt[w] = wt[w ^ (1 << hb)] + a[R + kLaneRoles + hb];
-            }
-            *reinterpret_cast<uint4*>(c + 32) = make_uint4(wt[0] * 0x10001u, wt[1] * 0x10001u, wt[2] * 0x10001u, wt[3] * 0x10001u);
-            *reinterpret_cast<uint4*>(c + 36) = make_uint4(wt[4] * 0x10001u, wt[5] * 0x10001u, wt[6] * 0x10001u, wt[7] * 0x10001u);
-            uint32_t tp[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-            for (int j = 0; j < R - 1; j++) tp[j] = a[1 + j] * 0x10001u;
-            *reinterpret_cast<uint4*>(c + 40) = make_uint4(tp[0], tp[1], tp[2], tp[3]);
-            *reinterpret_cast<uint4*>(c + 44) = make_uint4(tp[4], tp[5], tp[6], tp[7]);
-          } else {
-            // padding conformation: every score 0, below every real (biased) score
-#pragma unroll
-            for (int k = 0; k < 48; k += 4) *reinterpret_cast<uint4*>(c + k) = make_uint4(0, 0, 0, 0);
-          }
-        }
-      }
-      waited[buf]++;
-      __syncthreads();
-      if (s_abort) break;
-      // raw[buf] has been read by every producer: prefetch tile t + 2 into it
-      if (t + 2 < p.ntiles) {
-        if (tid == 0)
-          bulk_load(rawbuf + buf * T * p.rec_words, p.rec + (size_t)(t + 2) * T * p.rec_words, raw_bytes, &bars[buf]);
-        issued[buf]++;
-      }
-
-      // ---- consumer: every thread, every conformation of the tile
+    prefetch_first_tiles<T>(in, rawbuf, bars, issued);
+    for (int t = 0; t < in.ntiles; t++) {
+      if (!produce_tile<K>(in, p.ctrl, t, rawbuf, coefbuf, bars, issued, waited, o, ehigh, nroles, &s_abort)) break;
+      const uint32_t* cbuf = coefbuf + (t & 1) * T * CSTRIDE;
 #pragma unroll 2
       for (int s = 0; s < T; s++) {
-        const uint32_t* cs = cbuf + s * kCStride;
-        const uint32_t b0 = cs[lane] + cs[32 + warp];
-        uint32_t tpv[8];
-        {
-          const uint4 q0 = *reinterpret_cast<const uint4*>(cs + 40);
-          tpv[0] = q0.x; tpv[1] = q0.y; tpv[2] = q0.z; tpv[3] = q0.w;
-          if (R - 1 > 4) {
-            const uint4 q1 = *reinterpret_cast<const uint4*>(cs + 44);
-            tpv[4] = q1.x; tpv[5] = q1.y; tpv[6] = q1.z; tpv[7] = q1.w;
-          }
-        }
-        uint32_t x[P];
-        x[0] = b0;
+        const uint32_t* cs = cbuf + s * CSTRIDE;
+        uint32_t tpv[K::TP_WORDS];
 #pragma unroll
-        for (int v = 1; v < P; v++) {
+        for (int j = 0; j < K::TP_WORDS; j += 4) {
+          const uint4 q = *reinterpret_cast<const uint4*>(cs + K::TP_OFF + j);
+          tpv[j] = q.x; tpv[j + 1] = q.y; tpv[j + 2] = q.z; tpv[j + 3] = q.w;
+        }
+        // subset sums over the tree roles (IMAD: x * one + a keeps them on the FMA pipe); the
+        // leaves (top tree bit set) use the fused add + max
+        uint32_t x[P / 2];
+        x[0] = cs[lane] * p.one + cs[K::WT_OFF + warp];
+#pragma unroll
+        for (int v = 1; v < P / 2; v++) {
           const int hb = 31 - __clz(v);
-          x[v] = x[v ^ (1 << hb)] + tpv[hb];
+          x[v] = x[v ^ (1 << hb)] * p.one + tpv[hb];
         }
 #pragma unroll
-        for (int v = 0; v < P; v++) tmax[v] = vmax2(tmax[v], x[v]);
+        for (int v = 0; v < P / 2; v++) {
+          tmax[v] = vmax2(tmax[v], x[v]);
+          tmax[v + P / 2] = __viaddmax_u16x2(x[v], tpv[R - 2], tmax[v + P / 2]);
+        }
       }
-      // ---- tile merge: best (doubled) with tie bit, and first tile reaching it
+      // tile merge: best (doubled) with tie bit, and first tile reaching it
       const uint32_t tpk = (uint32_t)t * 0x10001u;
 #pragma unroll
       for (int v = 0; v < P; v++) {
@@ -296,82 +319,129 @@ __global__ void __launch_bounds__(kThreads, 1) phenotype_kernel(const __grid_con
       }
     }
     if (s_abort) break;
-    __syncthreads();  // every warp is done with the coefficient buffers
 
-    // ---- epilogue: park the state in shared memory, resolve candidates per warp
-    uint32_t* st_best = smem;                 // [P][kThreads]
-    uint32_t* st_tile = smem + P * kThreads;  // [P][kThreads]
+    // ================= classify: a field stays a candidate (best >= 2) only if its
+    // minimum was reached in a single tile (or labels are wanted); others resolve to -1
+    int next_tile = 0x7FFFFFFF;
 #pragma unroll
     for (int v = 0; v < P; v++) {
-      st_best[v * kThreads + tid] = m1[v];
-      st_tile[v * kThreads + tid] = ts[v];
-    }
-    const bool want_aux = p.aux != nullptr;
-    const uint32_t role_hi = ((uint32_t)lane << R) | ((uint32_t)warp << (R + kLaneRoles));
-    const uint32_t role_mask = (1u << nroles) - 1u;
-    for (int v = 0; v < P; v++) {
-      const uint32_t mine_best = st_best[v * kThreads + tid];
-      const uint32_t mine_tile = st_tile[v * kThreads + tid];
-      int ph[2] = {-1, -1}, ax[2] = {-1, -1};
+      uint32_t mv = m1[v], tv = ts[v];
 #pragma unroll
       for (int h = 0; h < 2; h++) {
-        const uint32_t field = (mine_best >> (16 * h)) & 0xFFFFu;
+        const uint32_t field = (mv >> (16 * h)) & 0xFFFFu;
         const uint32_t rw = (uint32_t)h | ((uint32_t)v << 1) | role_hi;
-        const bool valid = nroles >= NROLE || (rw >> nroles) == 0u;
+        const bool valid = nroles >= kRoles || (rw >> nroles) == 0u;
         const bool cand = valid && field > 1u && (want_aux || !(field & 1u));
-        uint32_t mask = __ballot_sync(0xFFFFFFFFu, cand);
+        if (!cand) {
+          mv &= ~(0xFFFFu << (16 * h));
+          tv |= 0xFFFFu << (16 * h);
+        } else {
+          next_tile = min(next_tile, (int)((tv >> (16 * h)) & 0xFFFFu));
+        }
+      }
+      st_best[v * kThreads + tid] = mv;
+      st_tile[v * kThreads + tid] = tv;
+    }
+
+    // ================= pass 2: re-stage each tile and resolve the candidates whose best lies in it
+    prefetch_first_tiles<T>(in, rawbuf, bars, issued);
+    for (int t = 0; t < in.ntiles; t++) {
+      if (!produce_tile<K>(in, p.ctrl, t, rawbuf, coefbuf, bars, issued, waited, o, ehigh, nroles, &s_abort)) break;
+      if (!__any_sync(0xFFFFFFFFu, next_tile == t)) continue;
+      const uint32_t* cbuf = coefbuf + (t & 1) * T * CSTRIDE;
+      bool need = next_tile == t;
+      while (__any_sync(0xFFFFFFFFu, need)) {
+        int f = -1;
+        uint32_t fld = 0;
+        if (need) {
+          for (int v = 0; v < P && f < 0; v++) {
+            const uint32_t mv = st_best[v * kThreads + tid], tv = st_tile[v * kThreads + tid];
+            for (int h = 0; h < 2; h++) {
+              const uint32_t fb = (mv >> (16 * h)) & 0xFFFFu;
+              if (f < 0 && fb >= 2u && ((tv >> (16 * h)) & 0xFFFFu) == (uint32_t)t) {
+                f = 2 * v + h;
+                fld = fb;
+              }
+            }
+          }
+          if (f < 0) need = false;
+        }
+        uint32_t mask = __ballot_sync(0xFFFFFFFFu, f >= 0);
         while (mask) {
           const int src = __ffs(mask) - 1;
           mask &= mask - 1;
-          const uint32_t sfield = __shfl_sync(0xFFFFFFFFu, field, src);
-          const int tile = (int)((__shfl_sync(0xFFFFFFFFu, mine_tile, src) >> (16 * h)) & 0xFFFFu);
-          const uint32_t rws = (uint32_t)h | ((uint32_t)v << 1) | ((uint32_t)src << R) | ((uint32_t)warp << (R + kLaneRoles));
-          const uint32_t eall = (rws & role_mask) | ehigh;
-          const uint32_t want = sfield & 0xFFFEu;
+          const int sf = __shfl_sync(0xFFFFFFFFu, f, src);
+          const uint32_t sfld = __shfl_sync(0xFFFFFFFFu, fld, src);
+          const int v = sf >> 1, h = sf & 1;
+          const uint32_t want = sfld & 0xFFFEu;
           int count = 0, first = -1;
           for (int i = 0; i < T; i += 32) {
-            const int s = tile * T + i + lane;
-            bool match = false;
-            if (s < p.S_dir) {
-              const uint32_t* r = p.rec + (size_t)s * p.rec_words;
-              uint32_t x = odd_part(r, p.NE, o);
-              for (uint32_t e = eall; e; e &= e - 1) x += coef(r[__ffs(e) - 1], o);
-              match = 2u * (x + 1u) == want;
-            }
+            const uint32_t* cs = cbuf + (i + lane) * CSTRIDE;
+            uint32_t x = cs[src] + cs[K::WT_OFF + warp];
+#pragma unroll
+            for (int j = 0; j < R - 1; j++)
+              if ((v >> j) & 1) x += cs[K::TP_OFF + j];
+            const bool match = ((x >> (16 * h)) & 0xFFFFu) == want;  // padding scores 0 never match
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, match);
-            if (first < 0 && bal) first = tile * T + i + __ffs(bal) - 1;
+            if (first < 0 && bal) first = t * T + i + __ffs(bal) - 1;
             count += __popc(bal);
           }
           if (lane == src) {
-            ax[h] = first >= 0 ? p.conf_class[first] : -1;
-            ph[h] = (!(sfield & 1u) && count == 1) ? ax[h] : -1;
+            const int cls = first >= 0 ? in.conf_class[first] : -1;
+            const bool unique = !(sfld & 1u) && count == 1;
+            const uint32_t sh = 16 * h;
+            st_best[v * kThreads + tid] = (st_best[v * kThreads + tid] & ~(0xFFFFu << sh)) | ((unique ? 1u : 0u) << sh);
+            st_tile[v * kThreads + tid] =
+                (st_tile[v * kThreads + tid] & ~(0xFFFFu << sh)) | (((uint32_t)cls & 0xFFFFu) << sh);
           }
+          __syncwarp();
         }
       }
-      // write the two sequences of this packed register (ids differ in bit 0)
-      const uint32_t rw0 = ((uint32_t)v << 1) | role_hi;
-      const bool valid0 = nroles >= NROLE || (rw0 >> nroles) == 0u;
-      const bool valid1 = nroles >= NROLE || ((rw0 | 1u) >> nroles) == 0u;
-      if (valid0) {
-        const uint32_t e0 = (rw0 & role_mask) | ehigh;
-        const unsigned long long g0 = interleave(e0, o);
-        const unsigned long long idx = bd.out_off + (g0 - bd.g_base);
-        const bool pair_ok = valid1 && ((reinterpret_cast<uintptr_t>(p.phen + idx) & 7u) == 0u) &&
-                             (!want_aux || (reinterpret_cast<uintptr_t>(p.aux + idx) & 7u) == 0u);
-        if (pair_ok) {
-          *reinterpret_cast<int2*>(p.phen + idx) = make_int2(ph[0], ph[1]);
-          if (want_aux) *reinterpret_cast<int2*>(p.aux + idx) = make_int2(ax[0], ax[1]);
-        } else {
-          p.phen[idx] = ph[0];
-          if (want_aux) p.aux[idx] = ax[0];
-          if (valid1) {
-            p.phen[idx + 1] = ph[1];
-            if (want_aux) p.aux[idx + 1] = ax[1];
-          }
+      if (next_tile == t) {
+        next_tile = 0x7FFFFFFF;
+        for (int v = 0; v < P; v++) {
+          const uint32_t mv = st_best[v * kThreads + tid], tv = st_tile[v * kThreads + tid];
+          for (int h = 0; h < 2; h++)
+            if (((mv >> (16 * h)) & 0xFFFFu) >= 2u) next_tile = min(next_tile, (int)((tv >> (16 * h)) & 0xFFFFu));
         }
       }
     }
-    __syncthreads();  // state area is reused as coefficient buffers by the next item
+    if (s_abort) break;
+
+    // ================= write the two sequences of each packed register (ids differ in bit 0)
+    for (int v = 0; v < P; v++) {
+      const uint32_t mv = st_best[v * kThreads + tid], tv = st_tile[v * kThreads + tid];
+      int ph[2], ax[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const uint32_t tf = (tv >> (16 * h)) & 0xFFFFu;
+        ax[h] = tf == 0xFFFFu ? -1 : (int)tf;
+        ph[h] = ((mv >> (16 * h)) & 0xFFFFu) == 1u ? ax[h] : -1;
+      }
+      const uint32_t rw0 = ((uint32_t)v << 1) | role_hi;
+      const bool valid0 = nroles >= kRoles || (rw0 >> nroles) == 0u;
+      const bool valid1 = nroles >= kRoles || ((rw0 | 1u) >> nroles) == 0u;
+      if (!valid0) continue;
+      const uint32_t e0 = (rw0 & role_mask) | ehigh;
+      const unsigned long long g0 = interleave(e0, o);
+      const unsigned long long idx = bd.out_off + (g0 - bd.g_base);
+      int32_t* ph_out = in.phen;
+      int32_t* ax_out = in.aux;
+      const bool pair_ok = valid1 && ((reinterpret_cast<uintptr_t>(ph_out + idx) & 7u) == 0u) &&
+                           (!want_aux || (reinterpret_cast<uintptr_t>(ax_out + idx) & 7u) == 0u);
+      if (pair_ok) {
+        *reinterpret_cast<int2*>(ph_out + idx) = make_int2(ph[0], ph[1]);
+        if (want_aux) *reinterpret_cast<int2*>(ax_out + idx) = make_int2(ax[0], ax[1]);
+      } else {
+        ph_out[idx] = ph[0];
+        if (want_aux) ax_out[idx] = ax[0];
+        if (valid1) {
+          ph_out[idx + 1] = ph[1];
+          if (want_aux) ax_out[idx + 1] = ax[1];
+        }
+      }
+    }
+    // the state area and s_item are rewritten by the next item (barriers at its top)
   }
   // after an abort, wait (bounded) for bulk copies still in flight before exiting
   if (tid == 0) {
@@ -383,28 +453,28 @@ __global__ void __launch_bounds__(kThreads, 1) phenotype_kernel(const __grid_con
   }
 }
 
-template <int R, int T>
-size_t smem_bytes(int rec_words) {
-  const size_t front = (size_t)Smem<R, T>::kCoefWords + 2ull * T * rec_words;
-  const size_t words = std::max(front, (size_t)Smem<R, T>::kStateWords);
-  return (((words + 3) & ~(size_t)3) * 4) + 2 * sizeof(uint64_t);
+template <class K>
+size_t smem_bytes(int max_rec_words) {
+  const size_t words = (size_t)K::kCoefWords + 2ull * K::T * max_rec_words + (size_t)K::kStateWords;
+  return words * 4 + 2 * sizeof(uint64_t);
 }
 
-template <int R, int T>
-int launch(const Params& prm, cudaStream_t stream) {
-  const size_t smem = smem_bytes<R, T>(prm.rec_words);
-  auto kern = phenotype_kernel<R, T>;
+template <class K>
+int launch_shape(const hp::PhenParams& prm, cudaStream_t stream, unsigned grid_limit) {
+  const size_t smem = smem_bytes<K>(prm.max_rec_words);
+  auto kern = phenotype_kernel<K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return hp::cuda_fail(e, "cudaFuncSetAttribute(phenotype_kernel)");
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::THREADS, smem);
   if (e != cudaSuccess) return hp::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  if (per_sm < 1) return hp::fail(HP_EUNSUPPORTED, "phenotype kernel does not fit on this GPU");
+  if (per_sm < 1) return hp::fail(HP_EUNSUPPORTED, "phenotype kernel shape does not fit on this GPU");
   unsigned long long grid = (unsigned long long)sms * per_sm;
   if (grid > prm.total_items) grid = prm.total_items;
-  kern<<<(unsigned)grid, kThreads, smem, stream>>>(prm);
+  if (grid_limit && grid > grid_limit) grid = grid_limit;
+  kern<<<(unsigned)grid, K::THREADS, smem, stream>>>(prm);
   e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "phenotype_kernel launch");
   return HP_OK;
@@ -414,35 +484,127 @@ int launch(const Params& prm, cudaStream_t stream) {
 
 namespace hp {
 
-// Split [begin, begin + count) into aligned power-of-two blocks and fill the
-// launch descriptors for a kernel with R register bits.
-int plan_blocks(const hp_structs* s, unsigned long long begin, unsigned long long count, int R, Params& prm) {
-  const int nrole_max = R + kLaneRoles + kWarpRoles;
-  unsigned long long pos = begin, end = begin + count, items = 0;
+bool tile_cfg_supported(int reg_bits, int tile) {
+  switch (reg_bits * 1000 + tile) {
+    case 4064: case 4128: case 5064: case 5128: case 5256: case 6064: case 6128: case 6256:
+      return true;
+    default:
+      return false;
+  }
+}
+
+void default_tile_cfg(int* reg_bits, int* tile) {
+  *reg_bits = 5;
+  *tile = 256;
+}
+
+int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit) {
+  switch (reg_bits * 1000 + tile) {
+    case 4064: return launch_shape<Cfg<4, 64>>(prm, stream, grid_limit);
+    case 4128: return launch_shape<Cfg<4, 128>>(prm, stream, grid_limit);
+    case 5064: return launch_shape<Cfg<5, 64>>(prm, stream, grid_limit);
+    case 5128: return launch_shape<Cfg<5, 128>>(prm, stream, grid_limit);
+    case 5256: return launch_shape<Cfg<5, 256>>(prm, stream, grid_limit);
+    case 6064: return launch_shape<Cfg<6, 64>>(prm, stream, grid_limit);
+    case 6128: return launch_shape<Cfg<6, 128>>(prm, stream, grid_limit);
+    case 6256: return launch_shape<Cfg<6, 256>>(prm, stream, grid_limit);
+    default: return fail(HP_EINVAL, "unsupported tile configuration");
+  }
+}
+
+int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
+                   int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm) {
+  if (n < 1 || n > kPhenMaxInst)
+    return fail(HP_EINVAL, "a batch holds 1 to " + std::to_string(kPhenMaxInst) + " instances");
+  // instances with more conformations first, so the dynamic queue ends on cheap items
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  for (int i = 0; i < n; i++)
+    if (!libs[i] || !d_phen || !d_phen[i]) return fail(HP_EINVAL, "batch entry " + std::to_string(i) + ": NULL library or output");
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return libs[a]->S_dir > libs[b]->S_dir; });
+  prm.ninst = n;
+  prm.max_rec_words = 0;
+  prm.one = 1u;
+  unsigned long long items = 0;
   int nb = 0;
-  while (pos < end) {
-    int m = 0;
-    while (m < 63) {
-      const unsigned long long size = 1ull << (m + 1);
-      if ((pos & (size - 1)) != 0 || pos + size > end) break;
-      m++;
+  for (int q = 0; q < n; q++) {
+    const int i = order[q];
+    const hp_structs* s = libs[i];
+    if (s->N > 2 * kMaxHalf) return fail(HP_EUNSUPPORTED, "N > 40");
+    if (s->S >= 0xFFFF) return fail(HP_EUNSUPPORTED, "more than 65534 classes");
+    const unsigned long long space = 1ull << s->N;
+    if (begins[i] >= space || counts[i] > space - begins[i])
+      return fail(HP_EINVAL, "batch entry " + std::to_string(i) + ": sequence range exceeds 2^N");
+    DevTables* dt = nullptr;
+    int rc = device_tables(s, &dt);
+    if (rc != HP_OK) return rc;
+    PhenInst& in = prm.inst[q];
+    in.rec = dt->rec;
+    in.conf_class = dt->conf_class;
+    in.phen = d_phen[i];
+    in.aux = d_aux ? d_aux[i] : nullptr;
+    in.S_dir = s->S_dir;
+    in.ntiles = (s->S_dir + tile - 1) / tile;
+    in.rec_words = s->rec_words;
+    in.NE = s->NE;
+    prm.max_rec_words = std::max(prm.max_rec_words, s->rec_words);
+    // aligned power-of-two blocks of [begin, begin + count)
+    unsigned long long pos = begins[i], end = begins[i] + counts[i];
+    while (pos < end) {
+      int m = 0;
+      while (m < 63) {
+        const unsigned long long size = 1ull << (m + 1);
+        if ((pos & (size - 1)) != 0 || pos + size > end) break;
+        m++;
+      }
+      if (nb >= kPhenMaxBlocks) return fail(HP_EUNSUPPORTED, "sequence ranges split into too many aligned blocks");
+      PhenBlock& d = prm.blocks[nb++];
+      d.g_base = pos;
+      d.out_off = pos - begins[i];
+      d.item_begin = items;
+      d.ne_free = (unsigned)std::min((m + 1) / 2, s->NE);
+      d.no_free = (unsigned)std::min(m / 2, s->NO);
+      d.nroles = (unsigned)std::min((int)d.ne_free, kRoles);
+      d.inst = (unsigned)q;
+      items += (1ull << d.no_free) << (d.ne_free - d.nroles);
+      pos += 1ull << m;
     }
-    if (nb >= kMaxBlocks) return fail(HP_EUNSUPPORTED, "sequence range splits into too many aligned blocks");
-    BlockDesc& d = prm.blocks[nb++];
-    d.g_base = pos;
-    d.out_off = pos - begin;
-    d.item_begin = items;
-    d.ne_free = (unsigned)std::min((m + 1) / 2, s->NE);
-    d.no_free = (unsigned)std::min(m / 2, s->NO);
-    d.nroles = (unsigned)std::min((int)d.ne_free, nrole_max);
-    d.pad = 0;
-    const unsigned chunk_bits = d.ne_free - d.nroles;
-    items += (1ull << d.no_free) << chunk_bits;
-    pos += 1ull << m;
   }
   prm.nblocks = nb;
   prm.total_items = items;
   return HP_OK;
+}
+
+int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
+                  int32_t* const* d_phen, int32_t* const* d_aux, int reg_bits, int tile, cudaStream_t st,
+                  unsigned grid_limit) {
+  if (!tile_cfg_supported(reg_bits, tile)) return fail(HP_EINVAL, "unsupported tile configuration");
+  PhenParams* prm = new (std::nothrow) PhenParams();
+  if (!prm) return fail(HP_ENOMEM, "out of host memory");
+  int rc = plan_phenotype(libs, begins, counts, n, d_phen, d_aux, tile, *prm);
+  if (rc != HP_OK || prm->total_items == 0) {
+    delete prm;
+    return rc;
+  }
+  unsigned* ctrl = nullptr;
+  cudaError_t e = cudaMallocAsync(&ctrl, kPhenCtrlBytes, st);
+  if (e != cudaSuccess) {
+    delete prm;
+    return cuda_fail(e, "cudaMallocAsync(phenotype control words)");
+  }
+  cudaMemsetAsync(ctrl, 0, kPhenCtrlBytes, st);
+  prm->ctrl = ctrl;
+  rc = launch_phenotype(*prm, reg_bits, tile, st, grid_limit);
+  delete prm;
+  unsigned herr = 0;
+  if (rc == HP_OK) {
+    e = cudaMemcpyAsync(&herr, ctrl, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "phenotype kernel execution");
+  }
+  cudaFreeAsync(ctrl, st);
+  if (rc == HP_OK && (herr & kErrTimeout)) rc = fail(HP_ETIMEOUT, "phenotype kernel: a bulk-copy wait timed out");
+  return rc;
 }
 
 }  // namespace hp
@@ -453,49 +615,12 @@ extern "C" int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_
   if (!d_phen) return hp::fail(HP_EINVAL, "hp_phenotype_map: d_phen is NULL");
   if (gap_threshold != 1) return hp::fail(HP_EUNSUPPORTED, "hp_phenotype_map: only gap_threshold 1 is implemented");
   if (s->N > 2 * hp::kMaxHalf) return hp::fail(HP_EUNSUPPORTED, "hp_phenotype_map: N > 40");
-  const unsigned long long space = s->N >= 64 ? ~0ull : (1ull << s->N);
   if (seq_count == 0) return HP_OK;
+  const unsigned long long space = 1ull << s->N;
   if (seq_begin >= space || seq_count > space - seq_begin)
     return hp::fail(HP_EINVAL, "hp_phenotype_map: sequence range exceeds 2^N");
-  hp::DevTables* dt = nullptr;
-  int rc = hp::device_tables(s, &dt);
-  if (rc != HP_OK) return rc;
-  constexpr int R = 6, T = 256;
-  static_assert(T % 4 == 0 && hp::kRecPad % T == 0, "tiles must tile the padded record table");
-  Params* prm = new (std::nothrow) Params();
-  if (!prm) return hp::fail(HP_ENOMEM, "hp_phenotype_map: out of host memory");
-  prm->rec = dt->rec;
-  prm->conf_class = dt->conf_class;
-  prm->phen = d_phen;
-  prm->aux = d_argmin_aux;
-  prm->S_dir = s->S_dir;
-  prm->ntiles = (s->S_dir + T - 1) / T;
-  prm->rec_words = s->rec_words;
-  prm->NE = s->NE;
-  prm->NO = s->NO;
-  rc = hp::plan_blocks(s, seq_begin, seq_count, R, *prm);
-  if (rc != HP_OK) {
-    delete prm;
-    return rc;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  unsigned int* err = nullptr;
-  cudaError_t e = cudaMallocAsync(&err, sizeof(unsigned int), st);
-  if (e != cudaSuccess) {
-    delete prm;
-    return hp::cuda_fail(e, "cudaMallocAsync(error word)");
-  }
-  cudaMemsetAsync(err, 0, sizeof(unsigned int), st);
-  prm->err = err;
-  rc = launch<R, T>(*prm, st);
-  delete prm;
-  unsigned int herr = 0;
-  if (rc == HP_OK) {
-    e = cudaMemcpyAsync(&herr, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_phenotype_map: kernel execution");
-  }
-  cudaFreeAsync(err, st);
-  if (rc == HP_OK && (herr & kErrTimeout)) rc = hp::fail(HP_ETIMEOUT, "hp_phenotype_map: a bulk-copy wait timed out");
-  return rc;
+  int r = s->tile_reg_bits, t = s->tile_size;
+  if (!r) hp::default_tile_cfg(&r, &t);
+  return hp::run_phenotype(&s, &seq_begin, &seq_count, 1, &d_phen, d_argmin_aux ? &d_argmin_aux : nullptr, r, t,
+                           (cudaStream_t)stream, 0);
 }

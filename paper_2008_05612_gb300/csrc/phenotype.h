@@ -1,0 +1,53 @@
+// Launch description of the phenotype kernel (shared by the single-box,
+// batched, graph-captured and autotuning entry points).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+constexpr int kPhenMaxInst = 8;      // boxes per launch
+constexpr int kPhenMaxBlocks = 128;  // aligned id blocks per launch (all boxes)
+constexpr size_t kPhenCtrlBytes = 16;  // [0] error word, [2..3] work counter (64-bit)
+
+struct PhenInst {
+  const uint32_t* rec;       // conformation records, padded to a multiple of the tile
+  const int32_t* conf_class; // class of each conformation
+  int32_t* phen;             // output, indexed by id - begin
+  int32_t* aux;              // optional output (lowest-index minimiser's class)
+  int S_dir, ntiles, rec_words, NE;
+};
+
+struct PhenBlock {
+  unsigned long long g_base;      // first sequence id of the block (aligned to 2^m)
+  unsigned long long out_off;     // output index of g_base
+  unsigned long long item_begin;  // first work item of the block
+  unsigned int ne_free, no_free;  // even / odd residues below bit m
+  unsigned int nroles;            // real roles: min(ne_free, 14)
+  unsigned int inst;              // index into PhenParams::inst
+};
+
+struct PhenParams {
+  unsigned int* ctrl;  // kPhenCtrlBytes of device memory, zeroed before each launch
+  uint32_t one;        // always 1: tree additions are issued as x * one + a (IMAD)
+  int ninst, nblocks, max_rec_words;
+  unsigned long long total_items;
+  PhenInst inst[kPhenMaxInst];
+  PhenBlock blocks[kPhenMaxBlocks];
+};
+
+bool tile_cfg_supported(int reg_bits, int tile);
+void default_tile_cfg(int* reg_bits, int* tile);
+int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
+                   int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm);
+int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit);
+// plan + per-call control words + launch + error read-back (synchronises the stream)
+int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
+                  int32_t* const* d_phen, int32_t* const* d_aux, int reg_bits, int tile, cudaStream_t st,
+                  unsigned grid_limit);
+
+}  // namespace hp
