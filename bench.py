@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = "HP seq×struct evals/s & sequences/s (3x3x3, 6x6); learned-pruned vs plain"
 DIMS = (3, 3, 3)
 WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformations (51,704 classes)"
+# DRAM bytes (read + write) of one full 3x3x3 phenotype-kernel launch, from the ncu capture summarised in
+# profiles/phenotype_kernel_3x3x3.md (35.5 MB read + 502.1 MB written); set to None whenever the kernel
+# changes until it is captured again.
+TRAFFIC_PER_LAUNCH = 537_610_752
 
 
 def dist_env():
@@ -89,6 +93,24 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(value: float) -> float:
+    """Largest value over all ranks (the job's time is its slowest rank); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes units_per_rank per step (weak scaling)."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
 
 
 def measured_peaks():
@@ -248,15 +270,11 @@ def main():
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1))
     map_ms = [a.elapsed_time(b) for a, b in evs]
     ms_step = ms / args.steps
     evals_step = nseq * Sdir
-    value = world * evals_step / (ms_step * 1e-3)
+    value = job_value(evals_step, world, ms_step)
     hist = out[0].cpu().numpy()
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
@@ -288,9 +306,14 @@ def main():
     peaks = measured_peaks()
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak_ops = 128 * 152 * sm_max * 1e6  # lane-instructions issued per second: 4 SMSPs x 32 lanes per SM per clock
+    # ALU-pipe roofline of the phenotype kernel: every evaluation needs at least half a packed
+    # 16x2 max (two sequences per max.u16x2 / fused add+max), and the ALU pipe retires
+    # 64 lane-ops per clock per SM (16 lanes x 4 sub-partitions) on 152 SMs.
+    peak_ops = 64 * 152 * sm_max * 1e6
     map_avg_ms = float(np.mean(map_ms))
-    achieved = evals_step / (map_avg_ms * 1e-3)  # 1 packed lane-op (half an add + half a max) per evaluation
+    map_evals = evals_step / (map_avg_ms * 1e-3)
+    achieved = 0.5 * map_evals
+    tile_cfg = s.tile_cfg()
     line = {
         "metric": METRIC,
         "value": value,
@@ -310,18 +333,21 @@ def main():
                    "parallelism": "replicas" if world == 1 else f"replicas x{world}"},
         "sequences_per_s": world * nseq / (ms_step * 1e-3),
         "map_ms": map_avg_ms,
-        "map_evals_per_s": achieved,
+        "map_evals_per_s": map_evals,
+        "tile_cfg": {"reg_bits": tile_cfg[0], "tile": tile_cfg[1]},
         "fold_fraction": float(1.0 - hist[S] / nseq),
         "gpu_launches": args.steps * 8,
         "e2e": {"value": world * evals_step / (e2e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(d2h),
                 "note": "public Python API; outputs copied to pinned host memory inside the timed region; the only input "
                         "is the sequence range (no per-step input data)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "lane-ops/s",
-                     "frac": achieved / peak_ops, "traffic": None,
-                     "kernel": "phenotype_kernel<6,256>",
-                     "note": "1 packed 32-bit lane-op per evaluation (16-bit add + max, two sequences per op) vs the issue "
-                             "limit 128 lane-ops/clk/SM x 152 SMs x max SM clock"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "ALU lane-ops/s",
+                     "frac": achieved / peak_ops, "traffic": TRAFFIC_PER_LAUNCH,
+                     "kernel": f"phenotype_kernel<Cfg<{tile_cfg[0]},{tile_cfg[1]}>>",
+                     "peak_source": "derived: 64 ALU lane-ops/clk/SM x 152 SMs x max SM clock (no integer peak is measured "
+                                    "by the driver)",
+                     "note": "algorithmic ALU work = 0.5 packed max per sequence x conformation evaluation; achieved uses "
+                             "the map kernel's CUDA-event time inside the step"},
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
