@@ -134,6 +134,26 @@ int hp_batch_plan_launch(hp_batch_plan* plan, void* stream);
 int hp_batch_plan_status(hp_batch_plan* plan, void* stream);
 void hp_batch_plan_free(hp_batch_plan* plan);
 
+/* Ground state of an arbitrary list of sequence ids (e.g. a seeded sample,
+ * the paper's sampling mode of Table 3), one warp per sequence, with optional
+ * exact bound pruning seeded by candidate conformations (the learned
+ * proposal).  With A_s(h) = sum_i h_i c_i(s) and B the HH-contact count,
+ * -E = 10 A + 3 B <= 10 A + 3 min(C, floor(A/2)) (Eq. 1, Table 1 x 10); a
+ * conformation (or a whole tile of them, using per-tile maximum contact counts)
+ * whose bound is below the best exact score among the candidates is skipped.
+ * Skips are strict, so results equal the full scan's exactly.
+ *   d_ids:      device uint64[n] sequence ids (< 2^N);
+ *   d_cand:     device int32[n * k] candidate conformation indices (canonical
+ *               order, -1 = none) or NULL for the plain full scan;
+ *   d_phen:     device int32[n] phenotypes; d_aux: device int32[n] class of
+ *               the lowest-index minimum (or NULL);
+ *   d_counters: device uint64[2] (or NULL): conformations evaluated exactly
+ *               and conformation bounds evaluated are ADDED to [0] and [1].
+ * Stream-ordered; does not synchronise.  No counterpart in the paper beyond
+ * its sampled kernel (Appendix C). */
+int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand, int32_t k,
+                     int32_t* d_phen, int32_t* d_aux, uint64_t* d_counters, void* stream);
+
 /* Designability (Section 2.3): d_hist[p] = #{k : d_phen[k] = p} for
  * p in [0, S), d_hist[S] = #{k : d_phen[k] = -1}.
  *   d_phen: device int32[count], entries in [-1, S); d_hist: device

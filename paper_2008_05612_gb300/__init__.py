@@ -25,7 +25,7 @@ EXPORTS = (
     "hp_enumerate_structures", "hp_structs_info", "hp_structs_export", "hp_structs_free",
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
     "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
-    "hp_batch_plan_free", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
+    "hp_batch_plan_free", "hp_sequence_scan", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
     "hp_last_error",
 )
 _VOID = ("hp_structs_free", "hp_last_error", "hp_batch_plan_free")
@@ -71,6 +71,7 @@ def lib():
         L.hp_batch_plan_create.argtypes = [vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
         L.hp_batch_plan_launch.argtypes = [vp, vp]
         L.hp_batch_plan_status.argtypes = [vp, vp]
+        L.hp_sequence_scan.argtypes = [vp, vp, ctypes.c_int64, vp, i32, vp, vp, vp, vp]
         L.hp_batch_plan_free.argtypes = [vp]
         L.hp_batch_plan_free.restype = None
         L.hp_designability.argtypes = [vp, u64, i32, vp, vp]
@@ -237,6 +238,31 @@ class BatchPlan:
         if h is not None and _lib is not None:
             _lib.hp_batch_plan_free(h)
             self._h = None
+
+
+def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, stream=None):
+    """Phenotypes of arbitrary ids (hp_sequence_scan); cand: int32 [n, k] candidate conformations or None.
+    Returns phen (and aux if requested); counters (int64[2] CUDA tensor) accumulates
+    (exact evaluations, bound evaluations)."""
+    import torch
+
+    n = ids.numel()
+    if ids.dtype != torch.int64:
+        raise TypeError("ids must be int64 (bit patterns of uint64 ids)")
+    phen = torch.empty(n, dtype=torch.int32, device=ids.device)
+    ax = torch.empty(n, dtype=torch.int32, device=ids.device) if aux else None
+    k = 0
+    pc = None
+    if cand is not None:
+        if cand.dim() != 2 or cand.shape[0] != n:
+            raise ValueError("cand must be [n, k]")
+        k = cand.shape[1]
+        pc = _dptr(cand, torch.int32, "cand")
+    _check(lib().hp_sequence_scan(structs.handle, ctypes.c_void_p(ids.data_ptr()), n, pc, k,
+                                  _dptr(phen, torch.int32, "phen"), _dptr(ax, torch.int32, "aux") if aux else None,
+                                  _dptr(counters, torch.int64, "counters") if counters is not None else None,
+                                  _stream_ptr(stream)))
+    return (phen, ax) if aux else phen
 
 
 def designability(phen, S: int, out=None, stream=None):

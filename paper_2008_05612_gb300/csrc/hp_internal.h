@@ -23,6 +23,13 @@ struct DevTables {
   int device = -1;
   uint32_t* rec = nullptr;       // S_pad x rec_words contact records
   int32_t* conf_class = nullptr; // S_dir class ids
+  // per-sequence scan tables (built on first use): records in scan order (conformations
+  // sorted by their contact-count vectors so that a tile's bound is tight), the original
+  // index of each, and per-tile bound masks
+  uint32_t* scan_rec = nullptr;  // S_pad x rec_words
+  int32_t* scan_idx = nullptr;   // S_pad (-1 for padding)
+  uint32_t* scan_tb = nullptr;   // ntiles x 8 words
+  int scan_tile = 0;
 };
 
 }  // namespace hp
@@ -47,6 +54,8 @@ struct hp_structs {
   //            (bit j = odd residue 2j+1)
   //   [NE+b]   for b < 3: bit b of the contact count of each odd residue,
   //            as a mask over odd residues
+  //   [NE+3+b] for b < 3: bit b of the contact count of each even residue,
+  //            as a mask over even residues (bit k = residue 2k)
   //   rest     zero padding
   int rec_words = 0;
   std::vector<uint32_t> rec;        // S_dir x rec_words
@@ -59,6 +68,8 @@ struct hp_structs {
 namespace hp {
 // Upload (once per device) and return the device tables for the current device.
 int device_tables(const hp_structs* s, DevTables** out);
+// Same, plus the per-sequence scan tables.
+int scan_tables(const hp_structs* s, DevTables** out);
 // Records are padded on the device to a multiple of this many conformations.
 constexpr int kRecPad = 256;
 }  // namespace hp

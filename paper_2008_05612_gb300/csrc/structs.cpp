@@ -267,7 +267,7 @@ extern "C" int hp_enumerate_structures(int ndim, const int32_t dims[3], hp_struc
     st->C = box_edges - (N - 1);
     int C = st->C;
     st->contacts.assign((size_t)Sdir * (C > 0 ? C : 1) * 2, 0);
-    st->rec_words = st->NE + 3;
+    st->rec_words = st->NE + 6;
     if (st->rec_words % 2 == 0) st->rec_words++;
     st->rec.assign((size_t)Sdir * st->rec_words, 0u);
     for (int64_t k = 0; k < Sdir; k++) {
@@ -306,6 +306,11 @@ extern "C" int hp_enumerate_structures(int ndim, const int32_t dims[3], hp_struc
       for (int j = 0; j < st->NO; j++)
         for (int b = 0; b < 3; b++)
           if ((codd[j] >> b) & 1) rec[st->NE + b] |= 1u << j;
+      for (int j = 0; j < st->NE; j++) {
+        const int ce = __builtin_popcount(rec[j]);
+        for (int b = 0; b < 3; b++)
+          if ((ce >> b) & 1) rec[st->NE + 3 + b] |= 1u << j;
+      }
     }
   } catch (const std::bad_alloc&) {
     delete st;
