@@ -154,6 +154,47 @@ void hp_batch_plan_free(hp_batch_plan* plan);
 int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand, int32_t k,
                      int32_t* d_phen, int32_t* d_aux, uint64_t* d_counters, void* stream);
 
+/* ---- Learned proposal (no counterpart in the paper).  A network
+ * N -> H1 -> H2 -> S (ReLU, softmax over the S classes) reads the bits of a
+ * sequence id (1 = H) and proposes likely ground-state classes; their
+ * conformations seed the exact bound pruning of hp_sequence_scan.  It never
+ * decides a phenotype.  Weights are fp32 masters with bf16 copies; every
+ * matrix product is a bf16 tensor-core GEMM with fp32 accumulation; training
+ * minimises the mean cross-entropy with Adam (beta 0.9 / 0.999, eps 1e-8). */
+typedef struct hp_mlp hp_mlp;
+
+/* Create a network on the current device.  H1, H2 multiples of 32; max_batch
+ * rows per step.  h_params[0..5] are host fp32 arrays W1 [H1 x N], b1 [H1],
+ * W2 [H2 x H1], b2 [H2], W3 [S x H2], b3 [S] (row-major), copied in. */
+int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32_t max_batch, const float* const* h_params,
+                  hp_mlp** out);
+void hp_mlp_free(hp_mlp* m);
+
+/* Gradients of the cross-entropy of n (<= max_batch) device ids and class
+ * labels without updating: the loss is the sum over rows whose label is not
+ * -1, divided by n; h_grads[0..5] (entries may
+ * be NULL) receive fp32 gradients in the layout of h_params; *h_loss (may be
+ * NULL) the mean loss.  Synchronises `stream` when anything is read back. */
+int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t* d_labels, int32_t n, float* const* h_grads,
+                     float* h_loss, void* stream);
+
+/* One Adam step on n (<= max_batch) ids / labels with learning rate lr; the
+ * mean loss before the step goes to *h_loss if non-NULL (synchronises). */
+int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t* d_labels, int32_t n, float lr, float* h_loss,
+                      void* stream);
+
+/* Logits (fp32, n x S row-major, device) of n <= max_batch ids. */
+int hp_mlp_logits(hp_mlp* m, const uint64_t* d_ids, int32_t n, float* d_logits, void* stream);
+
+/* The k (1..16) highest-scoring classes of each of n ids (ties toward the
+ * lower class), into device int32[n x k]; runs in chunks of max_batch. */
+int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t k, int32_t* d_top, void* stream);
+
+/* Expand classes (device int32[n x k], -1 allowed) into their conformations:
+ * d_cand[n x 2k], entry 2j + q = q-th conformation of class j or -1. */
+int hp_proposal_conformations(const hp_structs* s, const int32_t* d_top, int64_t n, int32_t k, int32_t* d_cand,
+                              void* stream);
+
 /* Designability (Section 2.3): d_hist[p] = #{k : d_phen[k] = p} for
  * p in [0, S), d_hist[S] = #{k : d_phen[k] = -1}.
  *   d_phen: device int32[count], entries in [-1, S); d_hist: device

@@ -25,10 +25,11 @@ EXPORTS = (
     "hp_enumerate_structures", "hp_structs_info", "hp_structs_export", "hp_structs_free",
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
     "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
-    "hp_batch_plan_free", "hp_sequence_scan", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
+    "hp_batch_plan_free", "hp_sequence_scan", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
+    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
     "hp_last_error",
 )
-_VOID = ("hp_structs_free", "hp_last_error", "hp_batch_plan_free")
+_VOID = ("hp_structs_free", "hp_last_error", "hp_batch_plan_free", "hp_mlp_free")
 
 
 class TileCfg(ctypes.Structure):
@@ -72,6 +73,14 @@ def lib():
         L.hp_batch_plan_launch.argtypes = [vp, vp]
         L.hp_batch_plan_status.argtypes = [vp, vp]
         L.hp_sequence_scan.argtypes = [vp, vp, ctypes.c_int64, vp, i32, vp, vp, vp, vp]
+        L.hp_mlp_create.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.POINTER(vp)]
+        L.hp_mlp_free.argtypes = [vp]
+        L.hp_mlp_free.restype = None
+        L.hp_mlp_gradients.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.hp_mlp_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp]
+        L.hp_mlp_logits.argtypes = [vp, vp, i32, vp, vp]
+        L.hp_mlp_topk.argtypes = [vp, vp, ctypes.c_int64, i32, vp, vp]
+        L.hp_proposal_conformations.argtypes = [vp, vp, ctypes.c_int64, i32, vp, vp]
         L.hp_batch_plan_free.argtypes = [vp]
         L.hp_batch_plan_free.restype = None
         L.hp_designability.argtypes = [vp, u64, i32, vp, vp]
@@ -263,6 +272,77 @@ def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, st
                                   _dptr(counters, torch.int64, "counters") if counters is not None else None,
                                   _stream_ptr(stream)))
     return (phen, ax) if aux else phen
+
+
+class MLP:
+    """The learned proposal network (hp_mlp_*): N -> H1 -> H2 -> S, ReLU, softmax; bf16 GEMMs, fp32 Adam."""
+
+    def __init__(self, N, H1, H2, S, max_batch, params):
+        """params: six float32 numpy arrays W1 [H1,N], b1, W2 [H2,H1], b2, W3 [S,H2], b3."""
+        self.N, self.H1, self.H2, self.S, self.max_batch = N, H1, H2, S, max_batch
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in params]
+        shapes = [(H1, N), (H1,), (H2, H1), (H2,), (S, H2), (S,)]
+        for a, sh in zip(arrs, shapes):
+            if a.shape != sh:
+                raise ValueError(f"parameter shape {a.shape} != {sh}")
+        ptrs = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in arrs])
+        h = ctypes.c_void_p()
+        _check(lib().hp_mlp_create(N, H1, H2, S, max_batch, ptrs, ctypes.byref(h)))
+        self._h = h
+        self._shapes = shapes
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.hp_mlp_free(h)
+            self._h = None
+
+    def gradients(self, ids, labels, stream=None):
+        """(mean loss, [six fp32 numpy gradients]) without updating."""
+        import torch
+
+        grads = [np.zeros(sh, dtype=np.float32) for sh in self._shapes]
+        ptrs = (ctypes.c_void_p * 6)(*[g.ctypes.data for g in grads])
+        loss = ctypes.c_float()
+        _check(lib().hp_mlp_gradients(self._h, ctypes.c_void_p(ids.data_ptr()), _dptr(labels, torch.int32, "labels"),
+                                      ids.numel(), ptrs, ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value, grads
+
+    def train_step(self, ids, labels, lr, want_loss=False, stream=None):
+        import torch
+
+        loss = ctypes.c_float()
+        _check(lib().hp_mlp_train_step(self._h, ctypes.c_void_p(ids.data_ptr()), _dptr(labels, torch.int32, "labels"),
+                                       ids.numel(), ctypes.c_float(lr), ctypes.byref(loss) if want_loss else None,
+                                       _stream_ptr(stream)))
+        return loss.value if want_loss else None
+
+    def logits(self, ids, stream=None):
+        import torch
+
+        out = torch.empty((ids.numel(), self.S), dtype=torch.float32, device=ids.device)
+        _check(lib().hp_mlp_logits(self._h, ctypes.c_void_p(ids.data_ptr()), ids.numel(), _dptr(out, torch.float32, "out"),
+                                   _stream_ptr(stream)))
+        return out
+
+    def topk(self, ids, k, stream=None):
+        import torch
+
+        out = torch.empty((ids.numel(), k), dtype=torch.int32, device=ids.device)
+        _check(lib().hp_mlp_topk(self._h, ctypes.c_void_p(ids.data_ptr()), ids.numel(), k, _dptr(out, torch.int32, "out"),
+                                 _stream_ptr(stream)))
+        return out
+
+
+def proposal_conformations(structs: Structs, top, stream=None):
+    """[n, k] classes -> [n, 2k] conformations (hp_proposal_conformations)."""
+    import torch
+
+    n, k = top.shape
+    cand = torch.empty((n, 2 * k), dtype=torch.int32, device=top.device)
+    _check(lib().hp_proposal_conformations(structs.handle, _dptr(top.contiguous(), torch.int32, "top"), n, k,
+                                           _dptr(cand, torch.int32, "cand"), _stream_ptr(stream)))
+    return cand
 
 
 def designability(phen, S: int, out=None, stream=None):

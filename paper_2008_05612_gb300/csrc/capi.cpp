@@ -83,6 +83,8 @@ extern "C" void hp_structs_free(hp_structs* s) {
       if (t->scan_rec) cudaFree(t->scan_rec);
       if (t->scan_idx) cudaFree(t->scan_idx);
       if (t->scan_tb) cudaFree(t->scan_tb);
+      if (t->class_first) cudaFree(t->class_first);
+      if (t->class_nconf) cudaFree(t->class_nconf);
     }
     delete t;
   }

@@ -30,6 +30,9 @@ struct DevTables {
   int32_t* scan_idx = nullptr;   // S_pad (-1 for padding)
   uint32_t* scan_tb = nullptr;   // ntiles x 8 words
   int scan_tile = 0;
+  // class -> first conformation index and number of conformations (built on first use)
+  int32_t* class_first = nullptr;
+  int32_t* class_nconf = nullptr;
 };
 
 }  // namespace hp

@@ -1,0 +1,604 @@
+// The learned proposal: an N -> H1 -> H2 -> S network (ReLU, softmax over the
+// S classes) on the bits of a sequence id, trained on phenotype maps that the
+// exhaustive kernel computes, whose top-k classes seed the bound-pruned scan.
+// The paper has no learned component; this only ever proposes candidates, it
+// never decides a phenotype.
+//
+// Kernels (all hand-written): a bf16 tensor-core GEMM C = A B^T with fp32
+// accumulation (mma.sync m16n8k16, ldmatrix, cp.async double buffering,
+// fused bias / ReLU epilogue), tiled bf16 transposes, softmax cross-entropy,
+// column sums, ReLU backward, Adam, id -> bit encoding and per-row top-k.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hp_internal.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------------ GEMM
+
+constexpr int BM = 128, BN = 128, BK = 32, SK = 40;  // SK: padded smem row (elements), 80 B
+
+struct Gemm {
+  const bf16* A;  // [M, K] row-major, row stride lda (elements, multiple of 8)
+  const bf16* B;  // [N, K] row-major, row stride ldb
+  int lda, ldb, M, N, K;  // K a multiple of 32
+  const float* bias;      // [N] or NULL
+  int relu;
+  float* Cf;  // [M, N] fp32 (row stride ldcf) or NULL
+  int ldcf;
+  bf16* Cb;   // [M, N] bf16 (row stride ldcb) or NULL
+  int ldcb;
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) gemm_tn(const Gemm g) {
+  __shared__ __align__(16) bf16 sA[2][BM * SK];
+  __shared__ __align__(16) bf16 sB[2][BN * SK];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 2, wn = warp & 3;  // warp tile: 64 rows x 32 columns
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
+
+  auto load = [&](int stage, int k0) {
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      const int c = tid + i * 256, row = c >> 2, kc = (c & 3) * 8;
+      const int gr = m0 + row, gn = n0 + row;
+      const bf16* pa = gr < g.M ? g.A + (size_t)gr * g.lda + k0 + kc : g.A;
+      const bf16* pb = gn < g.N ? g.B + (size_t)gn * g.ldb + k0 + kc : g.B;
+      cp_async16(&sA[stage][row * SK + kc], pa, gr < g.M ? 16 : 0);
+      cp_async16(&sB[stage][row * SK + kc], pb, gn < g.N ? 16 : 0);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  const int nk = g.K / BK;
+  load(0, 0);
+  for (int kt = 0; kt < nk; kt++) {
+    if (kt + 1 < nk) {
+      load((kt + 1) & 1, (kt + 1) * BK);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const bf16* a_s = sA[kt & 1];
+    const bf16* b_s = sB[kt & 1];
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      uint32_t af[4][4], bfr[2][4];
+#pragma unroll
+      for (int mi = 0; mi < 4; mi++)
+        ldsm_x4(af[mi], a_s + (wm * 64 + mi * 16 + (lane & 15)) * SK + kk + (lane >> 4) * 8);
+#pragma unroll
+      for (int nj = 0; nj < 2; nj++)
+        ldsm_x4(bfr[nj], b_s + (wn * 32 + nj * 16 + (lane >> 4) * 8 + (lane & 7)) * SK + kk + ((lane >> 3) & 1) * 8);
+#pragma unroll
+      for (int mi = 0; mi < 4; mi++)
+#pragma unroll
+        for (int ni = 0; ni < 4; ni++) mma_bf16(acc[mi][ni], af[mi], bfr[ni >> 1][(ni & 1) * 2], bfr[ni >> 1][(ni & 1) * 2 + 1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 4; mi++)
+#pragma unroll
+    for (int ni = 0; ni < 4; ni++) {
+      const int col = n0 + wn * 32 + ni * 8 + (lane & 3) * 2;
+#pragma unroll
+      for (int hrow = 0; hrow < 2; hrow++) {
+        const int row = m0 + wm * 64 + mi * 16 + (lane >> 2) + hrow * 8;
+        if (row >= g.M) continue;
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int c = col + q;
+          if (c >= g.N) continue;
+          float v = acc[mi][ni][hrow * 2 + q];
+          if (g.bias) v += g.bias[c];
+          if (g.relu) v = fmaxf(v, 0.f);
+          if (g.Cf) g.Cf[(size_t)row * g.ldcf + c] = v;
+          if (g.Cb) g.Cb[(size_t)row * g.ldcb + c] = __float2bfloat16(v);
+        }
+      }
+    }
+}
+
+// ------------------------------------------------------------------ small kernels
+
+// out[c, r] = in[r, c] for r < rows, c < cols; zero in [rows, out_cols) of each output row
+__global__ void transpose_bf16(const bf16* __restrict__ in, int ldin, int rows, int cols, bf16* __restrict__ out,
+                               int ldout, int out_cols) {
+  __shared__ bf16 tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = r0 + j, c = c0 + threadIdx.x;
+    tile[j][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ldin + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int c = c0 + j, r = r0 + threadIdx.x;
+    if (c < cols && r < out_cols) out[(size_t)c * ldout + r] = tile[threadIdx.x][j];
+  }
+}
+
+__global__ void cast_bf16(const float* __restrict__ in, bf16* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16(in[i]);
+}
+
+// X[b, i] = bit i of ids[b] (1 = H) for i < N, 0 for i in [N, Kin) and for rows b >= n
+__global__ void encode_bits(const unsigned long long* __restrict__ ids, int n, int rows, int N, int Kin, bf16* __restrict__ X) {
+  const int b = blockIdx.x * blockDim.y + threadIdx.y;
+  if (b >= rows) return;
+  const unsigned long long g = b < n ? ids[b] : 0ull;
+  for (int i = threadIdx.x; i < Kin; i += blockDim.x)
+    X[(size_t)b * Kin + i] = __float2bfloat16((b < n && i < N && ((g >> i) & 1ull)) ? 1.f : 0.f);
+}
+
+// One block per row: loss += logsumexp(z) - z[label]; dz = (softmax(z) - onehot) * scale (bf16,
+// zero in padding columns); rows with label < 0 get dz = 0 and no loss.
+__global__ void softmax_xent(const float* __restrict__ Z, int ldz, int S, const int32_t* __restrict__ labels,
+                             bf16* __restrict__ dZ, int lddz, int Spad, float scale, float* __restrict__ loss) {
+  const int row = blockIdx.x;
+  const float* z = Z + (size_t)row * ldz;
+  bf16* d = dZ + (size_t)row * lddz;
+  const int lab = labels[row];
+  __shared__ float red[32];
+  float m = -INFINITY;
+  for (int c = threadIdx.x; c < S; c += blockDim.x) m = fmaxf(m, z[c]);
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -INFINITY;
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  m = red[0];
+  __syncthreads();
+  float sum = 0.f;
+  for (int c = threadIdx.x; c < S; c += blockDim.x) sum += __expf(z[c] - m);
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  sum = red[0];
+  const float inv = 1.f / sum;
+  for (int c = threadIdx.x; c < Spad; c += blockDim.x) {
+    float v = 0.f;
+    if (lab >= 0 && c < S) v = (__expf(z[c] - m) * inv - (c == lab ? 1.f : 0.f)) * scale;
+    d[c] = __float2bfloat16(v);
+  }
+  if (threadIdx.x == 0 && lab >= 0) atomicAdd(loss, logf(sum) + m - z[lab]);
+}
+
+// out[c] = sum over rows of in[r, c] (bf16 in, fp32 out)
+__global__ void colsum_bf16(const bf16* __restrict__ in, int ld, int rows, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int r = 0; r < rows; r++) s += __bfloat162float(in[(size_t)r * ld + c]);
+  out[c] = s;
+}
+
+// dA = dH * (H > 0), fp32 in, bf16 out
+__global__ void relu_backward(const float* __restrict__ dH, const bf16* __restrict__ H, bf16* __restrict__ dA, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dA[i] = __float2bfloat16(__bfloat162float(H[i]) > 0.f ? dH[i] : 0.f);
+}
+
+__global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            bf16* __restrict__ wb, size_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16(wi);
+  }
+}
+
+// Per row, the k largest of z[0..S) (ties toward the lower index); one block per row.
+constexpr int kTopKMax = 16;
+__global__ void topk_rows(const float* __restrict__ Z, int ldz, int S, int k, int32_t* __restrict__ out) {
+  const int row = blockIdx.x;
+  const float* z = Z + (size_t)row * ldz;
+  float bv[kTopKMax];
+  int bi[kTopKMax];
+  for (int j = 0; j < k; j++) {
+    bv[j] = -INFINITY;
+    bi[j] = 0x7FFFFFFF;
+  }
+  for (int c = threadIdx.x; c < S; c += blockDim.x) {
+    const float v = z[c];
+    if (v > bv[k - 1] || (v == bv[k - 1] && c < bi[k - 1])) {
+      int j = k - 1;
+      while (j > 0 && (v > bv[j - 1] || (v == bv[j - 1] && c < bi[j - 1]))) {
+        bv[j] = bv[j - 1];
+        bi[j] = bi[j - 1];
+        j--;
+      }
+      bv[j] = v;
+      bi[j] = c;
+    }
+  }
+  __shared__ float sv[256 * kTopKMax];
+  __shared__ int si[256 * kTopKMax];
+  for (int j = 0; j < k; j++) {
+    sv[threadIdx.x * k + j] = bv[j];
+    si[threadIdx.x * k + j] = bi[j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < k; j++) {
+      bv[j] = -INFINITY;
+      bi[j] = 0x7FFFFFFF;
+    }
+    for (int t = 0; t < (int)blockDim.x * k; t++) {
+      const float v = sv[t];
+      const int c = si[t];
+      if (c == 0x7FFFFFFF) continue;
+      if (v > bv[k - 1] || (v == bv[k - 1] && c < bi[k - 1])) {
+        int j = k - 1;
+        while (j > 0 && (v > bv[j - 1] || (v == bv[j - 1] && c < bi[j - 1]))) {
+          bv[j] = bv[j - 1];
+          bi[j] = bi[j - 1];
+          j--;
+        }
+        bv[j] = v;
+        bi[j] = c;
+      }
+    }
+    for (int j = 0; j < k; j++) out[(size_t)row * k + j] = bi[j] < S ? bi[j] : -1;
+  }
+}
+
+// cand[r, 2j + q] = q-th conformation of class top[r, j] (or -1)
+__global__ void classes_to_conformations(const int32_t* __restrict__ top, long long n, int k,
+                                         const int32_t* __restrict__ first_conf, const int32_t* __restrict__ nconf,
+                                         int32_t* __restrict__ cand) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n * k) return;
+  const int c = top[i];
+  const int f = c >= 0 ? first_conf[c] : -1;
+  const int m = c >= 0 ? nconf[c] : 0;
+  cand[2 * i] = m > 0 ? f : -1;
+  cand[2 * i + 1] = m > 1 ? f + 1 : -1;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ model
+
+struct hp_mlp {
+  int N, H1, H2, S, Kin, Spad, max_batch;
+  int device = -1;
+  // parameters: fp32 master copies, bf16 working copies, Adam moments, gradients
+  float *w[6] = {nullptr}, *g[6] = {nullptr}, *m[6] = {nullptr}, *v[6] = {nullptr};
+  size_t n[6] = {0};
+  bf16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr, *w2t = nullptr, *w3t = nullptr;
+  // activations / workspaces for max_batch rows (Bp = max_batch rounded to 32)
+  bf16 *X = nullptr, *XT = nullptr, *Hb1 = nullptr, *Hb2 = nullptr, *H1T = nullptr, *H2T = nullptr;
+  float *Z = nullptr, *dHf = nullptr, *loss = nullptr;
+  bf16 *dZ = nullptr, *dZT = nullptr, *dA2 = nullptr, *dA2T = nullptr, *dA1 = nullptr, *dA1T = nullptr;
+  int32_t* labels = nullptr;
+  int steps = 0;
+};
+
+namespace {
+
+int gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const float* bias, int relu, float* Cf,
+         int ldcf, bf16* Cb, int ldcb, cudaStream_t st) {
+  if (K % BK != 0 || lda % 8 != 0 || ldb % 8 != 0) return hp::fail(HP_EINVAL, "gemm: K must be a multiple of 32");
+  Gemm g{A, B, lda, ldb, M, N, K, bias, relu, Cf, ldcf, Cb, ldcb};
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  gemm_tn<<<grid, 256, 0, st>>>(g);
+  return HP_OK;
+}
+
+void transpose(const bf16* in, int ldin, int rows, int cols, bf16* out, int ldout, int out_cols, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (std::max(rows, out_cols) + 31) / 32);
+  transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(in, ldin, rows, cols, out, ldout, out_cols);
+}
+
+int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
+
+// Forward pass for rows [0, rows) whose ids are in `ids` (n valid): logits -> m->Z
+void forward(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
+  encode_bits<<<(rows + 7) / 8, dim3(32, 8), 0, st>>>(ids, n, rows, m->N, m->Kin, m->X);
+  gemm(m->X, m->Kin, m->w1b, m->Kin, rows, m->H1, m->Kin, m->w[1], 1, nullptr, 0, m->Hb1, m->H1, st);
+  gemm(m->Hb1, m->H1, m->w2b, m->H1, rows, m->H2, m->H1, m->w[3], 1, nullptr, 0, m->Hb2, m->H2, st);
+  gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, m->w[5], 0, m->Z, m->Spad, nullptr, 0, st);
+}
+
+// Gradients of the mean cross-entropy over the n valid rows into m->g[*]; loss sum into m->loss
+void backward(hp_mlp* m, int n, int rows, cudaStream_t st) {
+  const int S = m->S, H1 = m->H1, H2 = m->H2, Kin = m->Kin, Spad = m->Spad;
+  cudaMemsetAsync(m->loss, 0, sizeof(float), st);
+  softmax_xent<<<rows, 256, 0, st>>>(m->Z, Spad, S, m->labels, m->dZ, Spad, Spad, 1.f / (float)std::max(n, 1), m->loss);
+  // layer 3
+  colsum_bf16<<<(S + 255) / 256, 256, 0, st>>>(m->dZ, Spad, rows, S, m->g[5]);
+  transpose(m->dZ, Spad, rows, Spad, m->dZT, rows, rows, st);
+  transpose(m->Hb2, H2, rows, H2, m->H2T, rows, rows, st);
+  gemm(m->dZT, rows, m->H2T, rows, S, H2, rows, nullptr, 0, m->g[4], H2, nullptr, 0, st);
+  gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, nullptr, 0, m->dHf, H2, nullptr, 0, st);
+  relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->dHf, m->Hb2, m->dA2, (size_t)rows * H2);
+  // layer 2
+  colsum_bf16<<<(H2 + 255) / 256, 256, 0, st>>>(m->dA2, H2, rows, H2, m->g[3]);
+  transpose(m->dA2, H2, rows, H2, m->dA2T, rows, rows, st);
+  transpose(m->Hb1, H1, rows, H1, m->H1T, rows, rows, st);
+  gemm(m->dA2T, rows, m->H1T, rows, H2, H1, rows, nullptr, 0, m->g[2], H1, nullptr, 0, st);
+  gemm(m->dA2, H2, m->w2t, H2, rows, H1, H2, nullptr, 0, m->dHf, H1, nullptr, 0, st);
+  relu_backward<<<grid_for((size_t)rows * H1), 256, 0, st>>>(m->dHf, m->Hb1, m->dA1, (size_t)rows * H1);
+  // layer 1
+  colsum_bf16<<<(H1 + 255) / 256, 256, 0, st>>>(m->dA1, H1, rows, H1, m->g[1]);
+  transpose(m->dA1, H1, rows, H1, m->dA1T, rows, rows, st);
+  transpose(m->X, Kin, rows, Kin, m->XT, rows, rows, st);
+  gemm(m->dA1T, rows, m->XT, rows, H1, Kin, rows, nullptr, 0, m->g[0], Kin, nullptr, 0, st);
+}
+
+// refresh the bf16 copies and transposes used by the forward and backward GEMMs
+void refresh_copies(hp_mlp* m, cudaStream_t st) {
+  cast_bf16<<<grid_for(m->n[0]), 256, 0, st>>>(m->w[0], m->w1b, m->n[0]);
+  cast_bf16<<<grid_for(m->n[2]), 256, 0, st>>>(m->w[2], m->w2b, m->n[2]);
+  cast_bf16<<<grid_for(m->n[4]), 256, 0, st>>>(m->w[4], m->w3b, m->n[4]);
+  transpose(m->w2b, m->H1, m->H2, m->H1, m->w2t, m->H2, m->H2, st);
+  transpose(m->w3b, m->H2, m->S, m->H2, m->w3t, m->Spad, m->Spad, st);
+}
+
+void free_model(hp_mlp* m) {
+  if (!m) return;
+  for (int i = 0; i < 6; i++) {
+    cudaFree(m->w[i]);
+    cudaFree(m->g[i]);
+    cudaFree(m->m[i]);
+    cudaFree(m->v[i]);
+  }
+  void* ptrs[] = {m->w1b, m->w2b, m->w3b, m->w2t, m->w3t, m->X, m->XT, m->Hb1, m->Hb2, m->H1T, m->H2T, m->Z, m->dHf,
+                  m->loss, m->dZ, m->dZT, m->dA2, m->dA2T, m->dA1, m->dA1T, m->labels};
+  for (void* p : ptrs) cudaFree(p);
+  delete m;
+}
+
+}  // namespace
+
+extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32_t max_batch, const float* const* h_params,
+                             hp_mlp** out) {
+  if (!out) return hp::fail(HP_EINVAL, "hp_mlp_create: out is NULL");
+  *out = nullptr;
+  if (N < 1 || N > 64 || H1 < 32 || H2 < 32 || H1 % 32 || H2 % 32 || S < 1 || max_batch < 1 || !h_params)
+    return hp::fail(HP_EINVAL, "hp_mlp_create: bad sizes (hidden widths must be multiples of 32)");
+  hp_mlp* m = new (std::nothrow) hp_mlp();
+  if (!m) return hp::fail(HP_ENOMEM, "hp_mlp_create: out of host memory");
+  m->N = N;
+  m->H1 = H1;
+  m->H2 = H2;
+  m->S = S;
+  m->Kin = round_up(N, 32);
+  m->Spad = round_up(S, 32);
+  m->max_batch = round_up(max_batch, 32);
+  cudaGetDevice(&m->device);
+  const size_t B = m->max_batch;
+  // W1 [H1, Kin] (columns >= N zero), b1 [H1], W2 [H2, H1], b2 [H2], W3 [S, H2], b3 [S]
+  m->n[0] = (size_t)H1 * m->Kin;
+  m->n[1] = H1;
+  m->n[2] = (size_t)H2 * H1;
+  m->n[3] = H2;
+  m->n[4] = (size_t)S * H2;
+  m->n[5] = S;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 6 && e == cudaSuccess; i++) {
+    e = cudaMalloc(&m->w[i], m->n[i] * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->g[i], m->n[i] * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->m[i], m->n[i] * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->v[i], m->n[i] * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->m[i], 0, m->n[i] * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->v[i], 0, m->n[i] * 4);
+  }
+  auto al = [&](auto** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+  };
+  al(&m->w1b, m->n[0] * 2);
+  al(&m->w2b, m->n[2] * 2);
+  al(&m->w3b, m->n[4] * 2);
+  al(&m->w2t, (size_t)H1 * H2 * 2);
+  al(&m->w3t, (size_t)H2 * m->Spad * 2);
+  al(&m->X, B * m->Kin * 2);
+  al(&m->XT, (size_t)m->Kin * B * 2);
+  al(&m->Hb1, B * H1 * 2);
+  al(&m->Hb2, B * H2 * 2);
+  al(&m->H1T, (size_t)H1 * B * 2);
+  al(&m->H2T, (size_t)H2 * B * 2);
+  al(&m->Z, B * m->Spad * 4);
+  al(&m->dHf, B * std::max(H1, H2) * 4);
+  al(&m->loss, 4);
+  al(&m->dZ, B * m->Spad * 2);
+  al(&m->dZT, (size_t)m->Spad * B * 2);
+  al(&m->dA2, B * H2 * 2);
+  al(&m->dA2T, (size_t)H2 * B * 2);
+  al(&m->dA1, B * H1 * 2);
+  al(&m->dA1T, (size_t)H1 * B * 2);
+  al(&m->labels, B * 4);
+  if (e != cudaSuccess) {
+    free_model(m);
+    return hp::cuda_fail(e, "hp_mlp_create: device allocation");
+  }
+  // parameters from the host: W1 arrives as [H1, N] and is widened to [H1, Kin]
+  std::vector<float> w1((size_t)H1 * m->Kin, 0.f);
+  for (int r = 0; r < H1; r++)
+    for (int c = 0; c < N; c++) w1[(size_t)r * m->Kin + c] = h_params[0][(size_t)r * N + c];
+  e = cudaMemcpy(m->w[0], w1.data(), w1.size() * 4, cudaMemcpyHostToDevice);
+  for (int i = 1; i < 6 && e == cudaSuccess; i++) e = cudaMemcpy(m->w[i], h_params[i], m->n[i] * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_model(m);
+    return hp::cuda_fail(e, "hp_mlp_create: upload");
+  }
+  refresh_copies(m, nullptr);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_model(m);
+    return hp::cuda_fail(e, "hp_mlp_create");
+  }
+  *out = m;
+  return HP_OK;
+}
+
+extern "C" void hp_mlp_free(hp_mlp* m) { free_model(m); }
+
+extern "C" int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t* d_labels, int32_t n,
+                                 float* const* h_grads, float* h_loss, void* stream) {
+  if (!m || !d_ids || !d_labels) return hp::fail(HP_EINVAL, "hp_mlp_gradients: NULL argument");
+  if (n < 1 || n > m->max_batch) return hp::fail(HP_EINVAL, "hp_mlp_gradients: batch exceeds max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rows = round_up(n, 32);
+  cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
+  cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+  forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
+  backward(m, n, rows, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_gradients: launch");
+  if (h_grads) {
+    std::vector<float> g1(m->n[0]);
+    e = cudaMemcpyAsync(g1.data(), m->g[0], m->n[0] * 4, cudaMemcpyDeviceToHost, st);
+    for (int i = 1; i < 6 && e == cudaSuccess; i++)
+      if (h_grads[i]) e = cudaMemcpyAsync(h_grads[i], m->g[i], m->n[i] * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h_grads[0])
+      for (int r = 0; r < m->H1; r++)
+        for (int c = 0; c < m->N; c++) h_grads[0][(size_t)r * m->N + c] = g1[(size_t)r * m->Kin + c];
+  }
+  if (h_loss && e == cudaSuccess) {
+    float l = 0;
+    e = cudaMemcpyAsync(&l, m->loss, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *h_loss = l / (float)n;
+  }
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_gradients");
+  return HP_OK;
+}
+
+extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t* d_labels, int32_t n, float lr,
+                                 float* h_loss, void* stream) {
+  if (!m || !d_ids || !d_labels) return hp::fail(HP_EINVAL, "hp_mlp_train_step: NULL argument");
+  if (n < 1 || n > m->max_batch) return hp::fail(HP_EINVAL, "hp_mlp_train_step: batch exceeds max_batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rows = round_up(n, 32);
+  cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
+  cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+  forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
+  backward(m, n, rows, st);
+  m->steps++;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.f / (1.f - powf(b1, (float)m->steps)), c2 = 1.f / (1.f - powf(b2, (float)m->steps));
+  for (int i = 0; i < 6; i++)
+    adam_update<<<grid_for(m->n[i]), 256, 0, st>>>(m->w[i], m->g[i], m->m[i], m->v[i], nullptr, m->n[i], lr, b1, b2, eps,
+                                                     c1, c2);
+  refresh_copies(m, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_train_step: launch");
+  if (h_loss) {
+    float l = 0;
+    e = cudaMemcpyAsync(&l, m->loss, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_train_step");
+    *h_loss = l / (float)n;
+  }
+  return HP_OK;
+}
+
+extern "C" int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t k, int32_t* d_top, void* stream) {
+  if (!m || !d_ids || !d_top) return hp::fail(HP_EINVAL, "hp_mlp_topk: NULL argument");
+  if (k < 1 || k > kTopKMax || k > m->S) return hp::fail(HP_EINVAL, "hp_mlp_topk: k must be in [1, 16] and <= S");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int64_t off = 0; off < n; off += m->max_batch) {
+    const int nb = (int)std::min<int64_t>(m->max_batch, n - off);
+    const int rows = round_up(nb, 32);
+    forward(m, reinterpret_cast<const unsigned long long*>(d_ids) + off, nb, rows, st);
+    topk_rows<<<nb, 256, 0, st>>>(m->Z, m->Spad, m->S, k, d_top + off * k);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_topk: launch");
+  return HP_OK;
+}
+
+extern "C" int hp_mlp_logits(hp_mlp* m, const uint64_t* d_ids, int32_t n, float* d_logits, void* stream) {
+  if (!m || !d_ids || !d_logits || n < 1 || n > m->max_batch) return hp::fail(HP_EINVAL, "hp_mlp_logits: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, round_up(n, 32), st);
+  cudaError_t e = cudaMemcpy2DAsync(d_logits, (size_t)m->S * 4, m->Z, (size_t)m->Spad * 4, (size_t)m->S * 4, n,
+                                    cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_logits");
+  return HP_OK;
+}
+
+extern "C" int hp_proposal_conformations(const hp_structs* s, const int32_t* d_top, int64_t n, int32_t k, int32_t* d_cand,
+                                         void* stream) {
+  if (!s || !d_top || !d_cand) return hp::fail(HP_EINVAL, "hp_proposal_conformations: NULL argument");
+  hp::DevTables* dt = nullptr;
+  int rc = hp::device_tables(s, &dt);
+  if (rc != HP_OK) return rc;
+  hp_structs* ms = const_cast<hp_structs*>(s);
+  std::lock_guard<std::mutex> lock(ms->mu);
+  if (!dt->class_first) {
+    std::vector<int32_t> first(s->S, -1), cnt(s->S, 0);
+    for (int32_t c = s->S_dir - 1; c >= 0; c--) {
+      first[s->conf_class[c]] = c;
+      cnt[s->conf_class[c]]++;
+    }
+    cudaError_t e = cudaMalloc(&dt->class_first, (size_t)s->S * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dt->class_nconf, (size_t)s->S * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(dt->class_first, first.data(), (size_t)s->S * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dt->class_nconf, cnt.data(), (size_t)s->S * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return hp::cuda_fail(e, "hp_proposal_conformations: class tables");
+  }
+  const long long total = n * (long long)k;
+  if (total > 0)
+    classes_to_conformations<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        d_top, n, k, dt->class_first, dt->class_nconf, d_cand);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_proposal_conformations: launch");
+  return HP_OK;
+}

@@ -1,0 +1,153 @@
+"""The learned proposal on the GPU: GEMM / forward against an fp64 reference on bf16-rounded
+operands, gradients against the oracle's fp64 network, training on labels from the exhaustive
+kernel, top-k, and what the trained network gains for the bound-pruned scan."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2008_05612_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# bf16 keeps 8 significant bits (unit roundoff u = 2^-8); operands of every product are rounded once,
+# sums are fp32, and an error passes through at most three layers: a normalised error of ~6u = 0.023
+# bounds the forward pass and the gradients; the tests allow 0.05.
+TOL = 0.05
+
+
+@pytest.fixture(scope="module")
+def hp():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2008_05612_gb300 as m
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA is not available for a gpu-marked test")
+    return m
+
+
+def init(N, H1, H2, S, seed):
+    return [inputs.init_weights((H1, N), N, seed), inputs.init_weights((H1,), N, seed + 1),
+            inputs.init_weights((H2, H1), H1, seed + 2), inputs.init_weights((H2,), H1, seed + 3),
+            inputs.init_weights((S, H2), H2, seed + 4), inputs.init_weights((S,), H2, seed + 5)]
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def ids_tensor(ids):
+    return torch.from_numpy(np.asarray(ids, dtype=np.uint64).view(np.int64)).cuda()
+
+
+@pytest.mark.parametrize("N,H1,H2,S,n", [(27, 64, 96, 300, 100), (36, 512, 512, 1000, 257)])
+def test_logits_match_fp64_reference(hp, N, H1, H2, S, n):
+    p = init(N, H1, H2, S, 11)
+    net = hp.MLP(N, H1, H2, S, 512, p)
+    ids = inputs.sample_ids(N, n, seed=3)
+    got = net.logits(ids_tensor(ids)).cpu().numpy().astype(np.float64)
+    x = omlp.bits(ids, N)
+    # reference with the bf16 roundings the GPU applies to operands and hidden activations
+    W1, b1, W2, b2, W3, b3 = p
+    a1 = bf16_round(np.maximum(x @ bf16_round(W1).T + b1, 0))
+    a2 = bf16_round(np.maximum(a1 @ bf16_round(W2).T + b2, 0))
+    want = a2 @ bf16_round(W3).T + b3
+    assert rel(got, want) < 1e-3
+    # and against the exact fp64 network, within the bf16 bound
+    assert rel(got, omlp.forward(p, x)[4]) < TOL
+
+
+def test_gradients_match_oracle(hp):
+    N, H1, H2, S, n = 27, 64, 64, 200, 96
+    p = init(N, H1, H2, S, 21)
+    net = hp.MLP(N, H1, H2, S, 128, p)
+    ids = inputs.sample_ids(N, n, seed=8)
+    labels = (inputs.splitmix64(ids) % np.uint64(S)).astype(np.int32)
+    loss, grads = net.gradients(ids_tensor(ids), torch.from_numpy(labels).cuda())
+    ref_loss, ref_grads = omlp.loss_and_grads([a.astype(np.float64) for a in p], omlp.bits(ids, N), labels.astype(np.int64))
+    assert abs(loss - ref_loss) < TOL * abs(ref_loss)
+    for g, r in zip(grads, ref_grads):
+        assert rel(g.astype(np.float64), r) < TOL
+
+
+def test_ignored_rows_do_not_contribute(hp):
+    N, H1, H2, S = 20, 32, 32, 50
+    p = init(N, H1, H2, S, 31)
+    net = hp.MLP(N, H1, H2, S, 64, p)
+    ids = inputs.sample_ids(N, 40, seed=9)
+    labels = (inputs.splitmix64(ids) % np.uint64(S)).astype(np.int32)
+    l1, g1 = net.gradients(ids_tensor(ids[:30]), torch.from_numpy(labels[:30]).cuda())
+    lab = labels.copy()
+    lab[30:] = -1
+    l2, g2 = net.gradients(ids_tensor(ids), torch.from_numpy(lab).cuda())
+    # the loss is the sum over labelled rows divided by the number of rows passed (40)
+    f = 30.0 / 40.0
+    assert abs(l2 - f * l1) < 1e-4 * abs(l1)
+    for a, b in zip(g1, g2):
+        # both are bf16-rounded products (the 1/n scale enters before the rounding): within ~2u
+        assert rel(b, f * a) < 1e-2 or np.abs(a).max() == 0
+
+
+def test_topk_matches_sorted_logits(hp):
+    N, H1, H2, S = 27, 64, 64, 700
+    net = hp.MLP(N, H1, H2, S, 512, init(N, H1, H2, S, 41))
+    ids = ids_tensor(inputs.sample_ids(N, 300, seed=4))
+    z = net.logits(ids).cpu().numpy()
+    top = net.topk(ids, 5).cpu().numpy()
+    want = np.argsort(-z, axis=1, kind="stable")[:, :5]
+    np.testing.assert_array_equal(top, want)
+
+
+@pytest.fixture(scope="module")
+def trained_3x3x3(hp):
+    """Network trained on the GPU with labels (lowest-index minimiser) from the exhaustive kernel,
+    on the seeded 1-in-10 sample of 3x3x3 ids restricted to a 2^20 block for test time."""
+    s = hp.Structs((3, 3, 3))
+    block = np.arange(1 << 20, dtype=np.uint64) * np.uint64(128) + np.uint64(37)  # spread over the space
+    train = block[inputs.training_mask(block)]
+    ids = ids_tensor(train)
+    # labels from the exhaustive kernel: map aligned 2^7-blocks would be wasteful; the per-sequence scan
+    # computes the same aux labels exactly for arbitrary ids
+    _, aux = hp.sequence_scan(s, ids, aux=True)
+    N, H1, H2, S = 27, 512, 512, s.S
+    p0 = init(N, H1, H2, S, 51)
+    net = hp.MLP(N, H1, H2, S, 1024, p0)
+    losses = []
+    perm = torch.randperm(ids.numel(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    for step in range(300):
+        j = perm[(step * 1024) % ids.numel():][:1024]
+        if j.numel() < 1024:
+            j = perm[:1024]
+        l = net.train_step(ids[j].contiguous(), aux[j].contiguous(), 1e-3, want_loss=(step % 50 == 0 or step == 299))
+        if l is not None:
+            losses.append(l)
+    return s, net, p0, losses
+
+
+def test_training_reduces_loss(trained_3x3x3):
+    _, _, _, losses = trained_3x3x3
+    assert losses[0] > 9.0  # about ln(51704) = 10.85 at initialisation
+    assert losses[-1] < losses[0] - 2.0
+
+
+def test_trained_proposal_prunes_more_than_untrained(hp, trained_3x3x3):
+    """What the network gains: the same exact phenotypes with fewer exact evaluations."""
+    s, net, p0, _ = trained_3x3x3
+    untrained = hp.MLP(27, 512, 512, s.S, 1024, p0)
+    ids = ids_tensor(inputs.sample_ids(27, 2048, seed=99))
+    plain = hp.sequence_scan(s, ids)
+    evals = {}
+    for name, model in (("trained", net), ("untrained", untrained)):
+        cand = hp.proposal_conformations(s, model.topk(ids, 4))
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+        phen = hp.sequence_scan(s, ids, cand=cand, counters=cnt)
+        assert torch.equal(phen, plain)
+        evals[name] = int(cnt[0])
+    print("exact evaluations:", evals, "plain:", 2048 * s.S_dir)
+    assert evals["trained"] < evals["untrained"] < 2048 * s.S_dir
