@@ -207,6 +207,85 @@ def run_map_only(args):
     return 0
 
 
+def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 1 << 16, k: int = 4,
+                batch: int = 4096, lr: float = 1e-3):
+    """Learned proposal + bound-pruned scan vs the plain per-sequence scan on the same seeded ids.
+
+    Labels: the lowest-index minimiser (aux output) of the exhaustive kernel's full map; training ids:
+    the seeded 1-in-10 sample of the whole space; network N -> 512 -> 512 -> S trained on the GPU with
+    the library's kernels.  Evaluation: `eval_n` seeded ids, timed with CUDA events: plain full scan vs
+    (network top-k + candidate expansion + pruned scan); phenotypes must agree exactly."""
+    from paper_2008_05612_gb300 import inputs
+
+    N, S = s.N, s.S
+    dev = "cuda"
+    phen = torch.empty(1 << N, dtype=torch.int32, device=dev)
+    aux = torch.empty(1 << N, dtype=torch.int32, device=dev)
+    hp.phenotype_map(s, 0, 1 << N, out=phen, aux=aux)
+    ids_all = np.arange(1 << N, dtype=np.uint64)
+    train_ids = ids_all[inputs.training_mask(ids_all)]
+    del ids_all
+    tids = torch.from_numpy(train_ids.view(np.int64)).to(dev)
+    tlab = aux[tids]
+    del phen, aux
+    params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
+              inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
+              inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
+    net = hp.MLP(N, 512, 512, S, batch, params)
+    untrained = hp.MLP(N, 512, 512, S, batch, params)
+    steps = max(1, int(train_fraction_epochs * tids.numel() / batch))
+    gen = torch.Generator(device=dev).manual_seed(0)
+    perm = torch.randperm(tids.numel(), device=dev, generator=gen)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    first_loss = last_loss = None
+    for st in range(steps):
+        j = perm[st * batch % (tids.numel() - batch):][:batch]
+        want = st == 0 or st == steps - 1
+        loss = net.train_step(tids[j].contiguous(), tlab[j].contiguous(), lr, want_loss=want)
+        if st == 0:
+            first_loss = loss
+        if st == steps - 1:
+            last_loss = loss
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    ev = torch.from_numpy(inputs.sample_ids(N, eval_n, seed=123).view(np.int64)).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / reps
+
+    plain, ms_plain = timed(lambda: hp.sequence_scan(s, ev))
+    res = {}
+    for name, model in (("trained", net), ("untrained", untrained)):
+        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+
+        def learned():
+            cand = hp.proposal_conformations(s, model.topk(ev, k))
+            return hp.sequence_scan(s, ev, cand=cand, counters=cnt)
+
+        out, ms = timed(learned)
+        _, ms_prop = timed(lambda: hp.proposal_conformations(s, model.topk(ev, k)))
+        exact = int(cnt[0]) / 4  # four calls accumulated (warm-up + 3 timed)
+        res[name] = {"ms": ms, "ms_proposal": ms_prop, "sequences_per_s": eval_n / (ms * 1e-3),
+                     "exact_eval_fraction": exact / (eval_n * s.S_dir),
+                     "mismatches_vs_plain": int((out != plain).sum().item())}
+    return {
+        "box": "3x3x3", "train_ids": int(tids.numel()), "train_steps": steps, "batch": batch, "lr": lr,
+        "train_s": train_s, "loss_first": first_loss, "loss_last": last_loss, "eval_ids": eval_n, "topk": k,
+        "plain_per_sequence": {"ms": ms_plain, "sequences_per_s": eval_n / (ms_plain * 1e-3)},
+        "learned_pruned": res["trained"], "untrained_pruned": res["untrained"],
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +293,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (one JSON line)")
     ap.add_argument("--map-only", default=None, metavar="BOX:BITS",
                     help="profiling case: only the phenotype map of ids [0, 2^BITS) of BOX (e.g. 6x6:27)")
     args = ap.parse_args()
@@ -237,6 +318,9 @@ def main():
 
     s = hp.Structs(DIMS)
     N, S, Sdir = s.N, s.S, s.S_dir
+    if args.learned_only:
+        print(json.dumps({"metric": METRIC, "learned": learned_leg(hp, s, torch)}))
+        return 0
     nseq = 1 << N
     stream = torch.cuda.current_stream()
     phen = torch.empty(nseq, dtype=torch.int32, device="cuda")
@@ -350,6 +434,11 @@ def main():
                              "the map kernel's CUDA-event time inside the step"},
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_learned:
+        try:
+            line["learned"] = learned_leg(hp, s, torch)
+        except Exception as exc:  # reported in the line, never hides the main measurement
+            line["learned"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(DIMS)
     if rank == 0:
