@@ -29,9 +29,8 @@ METRIC = "HP seq×struct evals/s & sequences/s (3x3x3, 6x6); learned-pruned vs p
 DIMS = (3, 3, 3)
 WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformations (51,704 classes)"
 # DRAM bytes (read + write) of one full 3x3x3 phenotype-kernel launch, from the ncu capture summarised in
-# profiles/phenotype_kernel_3x3x3.md (35.5 MB read + 502.1 MB written); set to None whenever the kernel
-# changes until it is captured again.
-TRAFFIC_PER_LAUNCH = 537_610_752
+# profiles/phenotype_kernel_3x3x3.md; None whenever the kernel has changed since the last capture.
+TRAFFIC_PER_LAUNCH = 1_769_066_752
 
 
 def dist_env():
@@ -111,6 +110,15 @@ def max_over_ranks(value: float) -> float:
 def job_value(units_per_rank: float, world: int, ms_per_step: float) -> float:
     """Whole-job throughput: every rank processes units_per_rank per step (weak scaling)."""
     return world * units_per_rank / (ms_per_step * 1e-3)
+
+
+def performed_sequences(N: int) -> int:
+    """Sequences the map kernel evaluates for the full space of an N-residue chain."""
+    if N % 2 == 0:
+        return 1 << N
+    no, ne = N // 2, N // 2 + 1
+    canonical = ((1 << no) + (1 << ((no + 1) // 2))) // 2  # odd patterns with o <= reverse(o)
+    return canonical << ne
 
 
 def measured_peaks():
@@ -396,7 +404,10 @@ def main():
     peak_ops = 64 * 152 * sm_max * 1e6
     map_avg_ms = float(np.mean(map_ms))
     map_evals = evals_step / (map_avg_ms * 1e-3)
-    achieved = 0.5 * map_evals
+    # evaluations the kernel actually performs: for an odd-length chain the full map is computed for one
+    # id of each reversal pair (odd-residue patterns o <= reverse(o)) and mirrored
+    performed = performed_sequences(N) * Sdir
+    achieved = 0.5 * performed / (map_avg_ms * 1e-3)
     tile_cfg = s.tile_cfg()
     line = {
         "metric": METRIC,
@@ -418,6 +429,7 @@ def main():
         "sequences_per_s": world * nseq / (ms_step * 1e-3),
         "map_ms": map_avg_ms,
         "map_evals_per_s": map_evals,
+        "map_performed_evals": performed,
         "tile_cfg": {"reg_bits": tile_cfg[0], "tile": tile_cfg[1]},
         "fold_fraction": float(1.0 - hist[S] / nseq),
         "gpu_launches": args.steps * 8,
@@ -430,8 +442,9 @@ def main():
                      "kernel": f"phenotype_kernel<Cfg<{tile_cfg[0]},{tile_cfg[1]}>>",
                      "peak_source": "derived: 64 ALU lane-ops/clk/SM x 152 SMs x max SM clock (no integer peak is measured "
                                     "by the driver)",
-                     "note": "algorithmic ALU work = 0.5 packed max per sequence x conformation evaluation; achieved uses "
-                             "the map kernel's CUDA-event time inside the step"},
+                     "note": "algorithmic ALU work = 0.5 packed max per performed sequence x conformation evaluation "
+                             "(odd chains: one id of each reversal pair, 50.8% of 2^27 for 3x3x3); achieved uses the "
+                             "map kernel's CUDA-event time inside the step"},
         "clocks": clocks,
     }
     if rank == 0 and not args.no_learned:

@@ -85,6 +85,7 @@ extern "C" void hp_structs_free(hp_structs* s) {
       if (t->scan_tb) cudaFree(t->scan_tb);
       if (t->class_first) cudaFree(t->class_first);
       if (t->class_nconf) cudaFree(t->class_nconf);
+      if (t->half_otab) cudaFree(t->half_otab);
     }
     delete t;
   }

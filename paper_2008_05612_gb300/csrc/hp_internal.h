@@ -33,6 +33,9 @@ struct DevTables {
   // class -> first conformation index and number of conformations (built on first use)
   int32_t* class_first = nullptr;
   int32_t* class_nconf = nullptr;
+  // odd-residue patterns o with o <= reverse(o) (odd N only; built on first use)
+  uint32_t* half_otab = nullptr;
+  int half_n = 0;
 };
 
 }  // namespace hp
@@ -73,6 +76,8 @@ namespace hp {
 int device_tables(const hp_structs* s, DevTables** out);
 // Same, plus the per-sequence scan tables.
 int scan_tables(const hp_structs* s, DevTables** out);
+// Same, plus the table of reversal-canonical odd patterns (odd N).
+int half_tables(const hp_structs* s, DevTables** out);
 // Records are padded on the device to a multiple of this many conformations.
 constexpr int kRecPad = 256;
 }  // namespace hp

@@ -267,8 +267,19 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     const hp::PhenBlock& bd = p.blocks[b];
     const hp::PhenInst& in = p.inst[bd.inst];
     const unsigned long long local = item - bd.item_begin;
-    const uint32_t o = odd_bits(bd.g_base) | (uint32_t)(local & ((1ull << bd.no_free) - 1));
-    const uint32_t chunk = (uint32_t)(local >> bd.no_free);
+    uint32_t o, chunk;
+    if (bd.otab) {
+      o = bd.otab[local % bd.ntab];
+      chunk = (uint32_t)(local / bd.ntab);
+    } else {
+      o = odd_bits(bd.g_base) | (uint32_t)(local & ((1ull << bd.no_free) - 1));
+      chunk = (uint32_t)(local >> bd.no_free);
+    }
+    // reversal mirror of this item's ids (only for non-palindromic odd patterns); when every free
+    // even residue is a role of this CTA, the mirrored ids are written in a second, coalesced pass
+    const uint32_t o_rev = bd.otab ? (__brev(o) >> (32 - bd.no_free)) : o;  // no_free >= 1 with a table
+    const bool mirror = bd.otab != nullptr && o_rev != o;
+    const bool mirror_gather = mirror && bd.ne_free == bd.nroles;
     const int nroles = (int)bd.nroles;
     const uint32_t ehigh = even_bits(bd.g_base) | (chunk << nroles);
     const uint32_t role_mask = (1u << nroles) - 1u;
@@ -427,6 +438,18 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       const unsigned long long idx = bd.out_off + (g0 - bd.g_base);
       int32_t* ph_out = in.phen;
       int32_t* ax_out = in.aux;
+      if (mirror && !mirror_gather) {
+        // P(h^R) = P(h) and the lowest minimising class is the same: write the reversed ids too
+        const uint32_t nbits_e = bd.ne_free;
+        const unsigned long long gm0 = interleave(__brev(e0) >> (32 - nbits_e), o_rev);
+        ph_out[bd.out_off + (gm0 - bd.g_base)] = ph[0];
+        if (want_aux) ax_out[bd.out_off + (gm0 - bd.g_base)] = ax[0];
+        if (valid1) {
+          const unsigned long long gm1 = interleave(__brev(e0 | 1u) >> (32 - nbits_e), o_rev);
+          ph_out[bd.out_off + (gm1 - bd.g_base)] = ph[1];
+          if (want_aux) ax_out[bd.out_off + (gm1 - bd.g_base)] = ax[1];
+        }
+      }
       const bool pair_ok = valid1 && ((reinterpret_cast<uintptr_t>(ph_out + idx) & 7u) == 0u) &&
                            (!want_aux || (reinterpret_cast<uintptr_t>(ax_out + idx) & 7u) == 0u);
       if (pair_ok) {
@@ -438,6 +461,46 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         if (valid1) {
           ph_out[idx + 1] = ph[1];
           if (want_aux) ax_out[idx + 1] = ax[1];
+        }
+      }
+    }
+    if (mirror_gather) {
+      // write id (rev(e), rev(o)) for this thread's own role pattern e; its result is the one of
+      // (rev(e), o) = roles of another thread, read from the shared-memory state
+      __syncthreads();
+      const int nbits_e = (int)bd.ne_free;
+      for (int v = 0; v < P; v++) {
+        int ph[2], ax[2];
+        const uint32_t rw0 = ((uint32_t)v << 1) | role_hi;
+        const bool valid0 = nroles >= kRoles || (rw0 >> nroles) == 0u;
+        const bool valid1 = nroles >= kRoles || ((rw0 | 1u) >> nroles) == 0u;
+        if (!valid0) continue;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const uint32_t src = __brev((rw0 | (uint32_t)h) & role_mask) >> (32 - nbits_e);  // roles of the source id
+          const uint32_t sh = src & 1u, sv = (src >> 1) & (uint32_t)(P - 1);
+          const uint32_t stid = ((src >> R) & 31u) + 32u * (src >> (R + kLaneRoles));
+          const uint32_t mv = st_best[sv * kThreads + stid], tv = st_tile[sv * kThreads + stid];
+          const uint32_t tf = (tv >> (16 * sh)) & 0xFFFFu;
+          ax[h] = tf == 0xFFFFu ? -1 : (int)tf;
+          ph[h] = ((mv >> (16 * sh)) & 0xFFFFu) == 1u ? ax[h] : -1;
+        }
+        const unsigned long long g0 = interleave(rw0 & role_mask, o_rev);
+        const unsigned long long idx = bd.out_off + (g0 - bd.g_base);
+        int32_t* ph_out = in.phen;
+        int32_t* ax_out = in.aux;
+        const bool pair_ok = valid1 && ((reinterpret_cast<uintptr_t>(ph_out + idx) & 7u) == 0u) &&
+                             (!want_aux || (reinterpret_cast<uintptr_t>(ax_out + idx) & 7u) == 0u);
+        if (pair_ok) {
+          *reinterpret_cast<int2*>(ph_out + idx) = make_int2(ph[0], ph[1]);
+          if (want_aux) *reinterpret_cast<int2*>(ax_out + idx) = make_int2(ax[0], ax[1]);
+        } else {
+          ph_out[idx] = ph[0];
+          if (want_aux) ax_out[idx] = ax[0];
+          if (valid1) {
+            ph_out[idx + 1] = ph[1];
+            if (want_aux) ax_out[idx + 1] = ax[1];
+          }
         }
       }
     }
@@ -512,6 +575,41 @@ int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t
   }
 }
 
+bool half_enumeration_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HP_FULL_ENUMERATION");
+    return !(e && e[0] == '1');
+  }();
+  return on;
+}
+
+int half_tables(const hp_structs* cs, DevTables** out) {
+  DevTables* dt = nullptr;
+  int rc = device_tables(cs, &dt);
+  if (rc != HP_OK) return rc;
+  hp_structs* s = const_cast<hp_structs*>(cs);
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (!dt->half_otab) {
+    const int no = s->NO;
+    std::vector<uint32_t> tab;
+    for (uint32_t o = 0; o < (1u << no); o++) {
+      uint32_t r = 0;
+      for (int j = 0; j < no; j++) r |= ((o >> j) & 1u) << (no - 1 - j);
+      if (o <= r) tab.push_back(o);
+    }
+    cudaError_t e = cudaMalloc(&dt->half_otab, tab.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(dt->half_otab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(dt->half_otab);
+      dt->half_otab = nullptr;
+      return cuda_fail(e, "reversal tables");
+    }
+    dt->half_n = (int)tab.size();
+  }
+  *out = dt;
+  return HP_OK;
+}
+
 int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
                    int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm) {
   if (n < 1 || n > kPhenMaxInst)
@@ -566,7 +664,20 @@ int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const 
       d.no_free = (unsigned)std::min(m / 2, s->NO);
       d.nroles = (unsigned)std::min((int)d.ne_free, kRoles);
       d.inst = (unsigned)q;
-      items += (1ull << d.no_free) << (d.ne_free - d.nroles);
+      d.otab = nullptr;
+      d.ntab = 0;
+      d.pad = 0;
+      if (m == s->N && (s->N & 1) && s->NO >= 1 && half_enumeration_enabled()) {
+        // the whole space of an odd-length chain: compute one id of every reversal pair
+        DevTables* ht = nullptr;
+        rc = half_tables(s, &ht);
+        if (rc != HP_OK) return rc;
+        d.otab = ht->half_otab;
+        d.ntab = (unsigned)ht->half_n;
+        items += (unsigned long long)d.ntab << (d.ne_free - d.nroles);
+      } else {
+        items += (1ull << d.no_free) << (d.ne_free - d.nroles);
+      }
       pos += 1ull << m;
     }
   }

@@ -29,6 +29,11 @@ struct PhenBlock {
   unsigned int ne_free, no_free;  // even / odd residues below bit m
   unsigned int nroles;            // real roles: min(ne_free, 14)
   unsigned int inst;              // index into PhenParams::inst
+  // reversal-symmetric half enumeration (full space of an odd-length chain): the odd
+  // patterns to compute (o <= reverse(o)); every result is also written at the reversed id
+  const uint32_t* otab;           // NULL: every odd pattern of the block
+  unsigned int ntab;              // entries of otab
+  unsigned int pad;
 };
 
 struct PhenParams {
