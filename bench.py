@@ -303,6 +303,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (one JSON line)")
+    ap.add_argument("--proposal-case", action="store_true",
+                    help="profiling case: top-4 proposals of an untrained 3x3x3 network for 65,536 ids, W + K times")
     ap.add_argument("--map-only", default=None, metavar="BOX:BITS",
                     help="profiling case: only the phenotype map of ids [0, 2^BITS) of BOX (e.g. 6x6:27)")
     args = ap.parse_args()
@@ -328,6 +330,25 @@ def main():
     N, S, Sdir = s.N, s.S, s.S_dir
     if args.learned_only:
         print(json.dumps({"metric": METRIC, "learned": learned_leg(hp, s, torch)}))
+        return 0
+    if args.proposal_case:
+        from paper_2008_05612_gb300 import inputs
+
+        params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
+                  inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
+                  inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
+        net = hp.MLP(N, 512, 512, S, 4096, params)
+        ev = torch.from_numpy(inputs.sample_ids(N, 1 << 16, seed=123).view(np.int64)).cuda()
+        for _ in range(args.warmup):
+            net.topk(ev, 4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            net.topk(ev, 4)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "proposal top-4, 65536 ids", "ms": e0.elapsed_time(e1) / args.steps}))
         return 0
     nseq = 1 << N
     stream = torch.cuda.current_stream()

@@ -134,6 +134,103 @@ __global__ void __launch_bounds__(256) gemm_tn(const Gemm g) {
     }
 }
 
+// Large-tile variant for the big products (the 512 x S output layer): BMxBN CTA tile, BK = 64,
+// STAGES-deep cp.async pipeline in dynamic shared memory, 8 warps of 64 x (BN/4) each.
+template <int BM_, int BN_, int STAGES>
+struct BigGemm {
+  static constexpr int BM = BM_, BN = BN_, BK = 64, SKB = BK + 8;  // padded row: 144 B (conflict-free ldmatrix)
+  static constexpr int WM = 64, WN = BN / 4;                          // 2 x 4 warps
+  static constexpr int MI = WM / 16, NI = WN / 8;
+  static constexpr size_t kStageElems = (size_t)(BM + BN) * SKB;
+  static constexpr size_t kSmemBytes = kStageElems * STAGES * sizeof(bf16);
+};
+
+template <int BM_, int BN_, int STAGES>
+__global__ void __launch_bounds__(256, 1) gemm_tn_big(const Gemm g) {
+  using C = BigGemm<BM_, BN_, STAGES>;
+  constexpr int BM = C::BM, BN = C::BN, BK = C::BK, SKB = C::SKB, MI = C::MI, NI = C::NI;
+  extern __shared__ __align__(16) bf16 smem_g[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp >> 2, wn = warp & 3;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[MI][NI][4];
+#pragma unroll
+  for (int i = 0; i < MI; i++)
+#pragma unroll
+    for (int j = 0; j < NI; j++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[i][j][q] = 0.f;
+  auto sa = [&](int st) { return smem_g + (size_t)st * C::kStageElems; };
+  auto sb = [&](int st) { return smem_g + (size_t)st * C::kStageElems + (size_t)BM * SKB; };
+  auto load = [&](int st, int k0) {
+    bf16* a_s = sa(st);
+    bf16* b_s = sb(st);
+    // BK = 64 elements = 8 chunks of 16 B per row
+    for (int c = tid; c < BM * 8; c += 256) {
+      const int row = c >> 3, kc = (c & 7) * 8, gr = m0 + row;
+      cp_async16(a_s + row * SKB + kc, gr < g.M ? g.A + (size_t)gr * g.lda + k0 + kc : g.A, gr < g.M ? 16 : 0);
+    }
+    for (int c = tid; c < BN * 8; c += 256) {
+      const int row = c >> 3, kc = (c & 7) * 8, gn = n0 + row;
+      cp_async16(b_s + row * SKB + kc, gn < g.N ? g.B + (size_t)gn * g.ldb + k0 + kc : g.B, gn < g.N ? 16 : 0);
+    }
+  };
+  const int nk = g.K / BK;
+#pragma unroll
+  for (int st = 0; st < STAGES - 1; st++) {
+    if (st < nk) load(st, st * BK);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int kt = 0; kt < nk; kt++) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 2) : "memory");
+    __syncthreads();
+    {
+      const int nxt = kt + STAGES - 1;
+      if (nxt < nk) load(nxt % STAGES, nxt * BK);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const bf16* a_s = sa(kt % STAGES);
+    const bf16* b_s = sb(kt % STAGES);
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      uint32_t af[MI][4], bfr[NI / 2][4];
+#pragma unroll
+      for (int mi = 0; mi < MI; mi++)
+        ldsm_x4(af[mi], a_s + (wm * 64 + mi * 16 + (lane & 15)) * SKB + kk + (lane >> 4) * 8);
+#pragma unroll
+      for (int nj = 0; nj < NI / 2; nj++)
+        ldsm_x4(bfr[nj], b_s + (wn * C::WN + nj * 16 + (lane >> 4) * 8 + (lane & 7)) * SKB + kk + ((lane >> 3) & 1) * 8);
+#pragma unroll
+      for (int mi = 0; mi < MI; mi++)
+#pragma unroll
+        for (int ni = 0; ni < NI; ni++)
+          mma_bf16(acc[mi][ni], af[mi], bfr[ni >> 1][(ni & 1) * 2], bfr[ni >> 1][(ni & 1) * 2 + 1]);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+  for (int mi = 0; mi < MI; mi++)
+#pragma unroll
+    for (int ni = 0; ni < NI; ni++) {
+      const int col = n0 + wn * C::WN + ni * 8 + (lane & 3) * 2;
+#pragma unroll
+      for (int hrow = 0; hrow < 2; hrow++) {
+        const int row = m0 + wm * 64 + mi * 16 + (lane >> 2) + hrow * 8;
+        if (row >= g.M) continue;
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int c = col + q;
+          if (c >= g.N) continue;
+          float v = acc[mi][ni][hrow * 2 + q];
+          if (g.bias) v += g.bias[c];
+          if (g.relu) v = fmaxf(v, 0.f);
+          if (g.Cf) g.Cf[(size_t)row * g.ldcf + c] = v;
+          if (g.Cb) g.Cb[(size_t)row * g.ldcb + c] = __float2bfloat16(v);
+        }
+      }
+    }
+}
+
 // ------------------------------------------------------------------ small kernels
 
 // out[c, r] = in[r, c] for r < rows, c < cols; zero in [rows, out_cols) of each output row
@@ -238,59 +335,73 @@ __global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, 
   }
 }
 
-// Per row, the k largest of z[0..S) (ties toward the lower index); one block per row.
 constexpr int kTopKMax = 16;
-__global__ void topk_rows(const float* __restrict__ Z, int ldz, int S, int k, int32_t* __restrict__ out) {
-  const int row = blockIdx.x;
+
+// Per row, the k <= KT largest of z[0..S) (ties toward the lower index); one warp per row.  Each
+// lane keeps a sorted list of its KT best over a strided, coalesced sweep; then k rounds select
+// the largest list head across the warp with shuffles.
+template <int KT>
+__global__ void topk_warp(const float* __restrict__ Z, int ldz, int S, int k, int rows, int32_t* __restrict__ out) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
   const float* z = Z + (size_t)row * ldz;
-  float bv[kTopKMax];
-  int bi[kTopKMax];
-  for (int j = 0; j < k; j++) {
+  float bv[KT];
+  int bi[KT];
+#pragma unroll
+  for (int j = 0; j < KT; j++) {
     bv[j] = -INFINITY;
     bi[j] = 0x7FFFFFFF;
   }
-  for (int c = threadIdx.x; c < S; c += blockDim.x) {
-    const float v = z[c];
-    if (v > bv[k - 1] || (v == bv[k - 1] && c < bi[k - 1])) {
-      int j = k - 1;
-      while (j > 0 && (v > bv[j - 1] || (v == bv[j - 1] && c < bi[j - 1]))) {
-        bv[j] = bv[j - 1];
-        bi[j] = bi[j - 1];
-        j--;
-      }
-      bv[j] = v;
-      bi[j] = c;
-    }
-  }
-  __shared__ float sv[256 * kTopKMax];
-  __shared__ int si[256 * kTopKMax];
-  for (int j = 0; j < k; j++) {
-    sv[threadIdx.x * k + j] = bv[j];
-    si[threadIdx.x * k + j] = bi[j];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < k; j++) {
-      bv[j] = -INFINITY;
-      bi[j] = 0x7FFFFFFF;
-    }
-    for (int t = 0; t < (int)blockDim.x * k; t++) {
-      const float v = sv[t];
-      const int c = si[t];
-      if (c == 0x7FFFFFFF) continue;
-      if (v > bv[k - 1] || (v == bv[k - 1] && c < bi[k - 1])) {
-        int j = k - 1;
-        while (j > 0 && (v > bv[j - 1] || (v == bv[j - 1] && c < bi[j - 1]))) {
-          bv[j] = bv[j - 1];
-          bi[j] = bi[j - 1];
-          j--;
-        }
-        bv[j] = v;
-        bi[j] = c;
+  for (int c = lane; c < S; c += 32) {
+    const float v = __ldcs(z + c);
+    if (v > bv[KT - 1]) {  // equal values arrive in increasing index per lane: keep the earlier one
+      // insertion into the sorted list (unrolled, branch-free moves)
+      float cv = v;
+      int ci = c;
+#pragma unroll
+      for (int j = 0; j < KT; j++) {
+        const bool take = cv > bv[j];
+        const float tv = bv[j];
+        const int ti = bi[j];
+        bv[j] = take ? cv : bv[j];
+        bi[j] = take ? ci : bi[j];
+        cv = take ? tv : cv;
+        ci = take ? ti : ci;
       }
     }
-    for (int j = 0; j < k; j++) out[(size_t)row * k + j] = bi[j] < S ? bi[j] : -1;
   }
+  for (int r = 0; r < k; r++) {
+    float v = bv[0];
+    int i = bi[0];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      const float ov = __shfl_xor_sync(0xFFFFFFFFu, v, off);
+      const int oi = __shfl_xor_sync(0xFFFFFFFFu, i, off);
+      if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+      }
+    }
+    if (lane == 0) out[(size_t)row * k + r] = i < S ? i : -1;
+    if (bi[0] == i) {  // the winning lane pops its head
+#pragma unroll
+      for (int j = 0; j < KT - 1; j++) {
+        bv[j] = bv[j + 1];
+        bi[j] = bi[j + 1];
+      }
+      bv[KT - 1] = -INFINITY;
+      bi[KT - 1] = 0x7FFFFFFF;
+    }
+  }
+}
+
+void launch_topk(const float* Z, int ldz, int S, int k, int rows, int32_t* out, cudaStream_t st) {
+  const dim3 block(256);
+  const dim3 grid((rows + 7) / 8);
+  if (k <= 4) topk_warp<4><<<grid, block, 0, st>>>(Z, ldz, S, k, rows, out);
+  else if (k <= 8) topk_warp<8><<<grid, block, 0, st>>>(Z, ldz, S, k, rows, out);
+  else topk_warp<16><<<grid, block, 0, st>>>(Z, ldz, S, k, rows, out);
 }
 
 // cand[r, 2j + q] = q-th conformation of class top[r, j] (or -1)
@@ -333,6 +444,13 @@ int gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, co
          int ldcf, bf16* Cb, int ldcb, cudaStream_t st) {
   if (K % BK != 0 || lda % 8 != 0 || ldb % 8 != 0) return hp::fail(HP_EINVAL, "gemm: K must be a multiple of 32");
   Gemm g{A, B, lda, ldb, M, N, K, bias, relu, Cf, ldcf, Cb, ldcb};
+  using Big = BigGemm<128, 256, 3>;
+  if (K % Big::BK == 0 && (long long)M * N >= (1ll << 22) && K >= 128) {
+    cudaFuncSetAttribute(gemm_tn_big<128, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Big::kSmemBytes);
+    dim3 grid((N + Big::BN - 1) / Big::BN, (M + Big::BM - 1) / Big::BM);
+    gemm_tn_big<128, 256, 3><<<grid, 256, Big::kSmemBytes, st>>>(g);
+    return HP_OK;
+  }
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
   gemm_tn<<<grid, 256, 0, st>>>(g);
   return HP_OK;
@@ -557,7 +675,7 @@ extern "C" int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t 
     const int nb = (int)std::min<int64_t>(m->max_batch, n - off);
     const int rows = round_up(nb, 32);
     forward(m, reinterpret_cast<const unsigned long long*>(d_ids) + off, nb, rows, st);
-    topk_rows<<<nb, 256, 0, st>>>(m->Z, m->Spad, m->S, k, d_top + off * k);
+    launch_topk(m->Z, m->Spad, m->S, k, nb, d_top + off * k, st);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_topk: launch");

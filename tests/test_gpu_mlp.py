@@ -46,7 +46,7 @@ def ids_tensor(ids):
     return torch.from_numpy(np.asarray(ids, dtype=np.uint64).view(np.int64)).cuda()
 
 
-@pytest.mark.parametrize("N,H1,H2,S,n", [(27, 64, 96, 300, 100), (36, 512, 512, 1000, 257)])
+@pytest.mark.parametrize("N,H1,H2,S,n", [(27, 64, 96, 300, 100), (36, 512, 512, 1000, 257), (27, 512, 512, 9000, 512)])
 def test_logits_match_fp64_reference(hp, N, H1, H2, S, n):
     p = init(N, H1, H2, S, 11)
     net = hp.MLP(N, H1, H2, S, 512, p)
@@ -63,17 +63,23 @@ def test_logits_match_fp64_reference(hp, N, H1, H2, S, n):
     assert rel(got, omlp.forward(p, x)[4]) < TOL
 
 
-def test_gradients_match_oracle(hp):
-    N, H1, H2, S, n = 27, 64, 64, 200, 96
+@pytest.mark.parametrize("N,H1,H2,S,n", [(27, 64, 64, 200, 96), (27, 512, 512, 8200, 512)])
+def test_gradients_match_oracle(hp, N, H1, H2, S, n):
+    """The second shape routes the output layer and its gradients through the large-tile GEMM."""
     p = init(N, H1, H2, S, 21)
-    net = hp.MLP(N, H1, H2, S, 128, p)
+    net = hp.MLP(N, H1, H2, S, max(128, n), p)
     ids = inputs.sample_ids(N, n, seed=8)
     labels = (inputs.splitmix64(ids) % np.uint64(S)).astype(np.int32)
     loss, grads = net.gradients(ids_tensor(ids), torch.from_numpy(labels).cuda())
-    ref_loss, ref_grads = omlp.loss_and_grads([a.astype(np.float64) for a in p], omlp.bits(ids, N), labels.astype(np.int64))
+    # reference: the oracle's fp64 network on the bf16-rounded weights the GPU multiplies with, so that
+    # parameter quantisation (which flips a few near-zero ReLU masks in wide layers) is not counted
+    # as arithmetic error
+    pr = [bf16_round(a) if a.ndim == 2 else a.astype(np.float64) for a in p]
+    ref_loss, ref_grads = omlp.loss_and_grads(pr, omlp.bits(ids, N), labels.astype(np.int64))
     assert abs(loss - ref_loss) < TOL * abs(ref_loss)
-    for g, r in zip(grads, ref_grads):
-        assert rel(g.astype(np.float64), r) < TOL
+    errs = [rel(g.astype(np.float64), r) for g, r in zip(grads, ref_grads)]
+    print("gradient errors (W1 b1 W2 b2 W3 b3):", ["%.4f" % e for e in errs])
+    assert max(errs) < TOL
 
 
 def test_ignored_rows_do_not_contribute(hp):
