@@ -185,6 +185,65 @@ def run_reference(args):
     return 0
 
 
+def map_statistics(hist, neutral, to_del, N, S):
+    """Section 3.2 statistics of a whole-space map from exact counters (index S is -1)."""
+    hist = hist.astype(np.int64)
+    neutral = neutral.astype(np.int64)
+    to_del = to_del.astype(np.int64)
+    total = int(hist.sum())
+    d = hist[:S] > 0
+    Np = hist[:S][d].astype(np.float64)
+    rho = neutral[:S][d] / (N * Np)
+    phid = to_del[:S][d] / (N * Np)
+    other = 1.0 - rho - phid
+    flips_other = N * int(hist[:S].sum()) - int(neutral[:S].sum()) - int(to_del[:S].sum())
+    return {
+        "sequences": total,
+        "fold_fraction": 1.0 - hist[S] / total,
+        "designable": int(d.sum()),
+        "classes": S,
+        "top_designability": int(hist[:S].max()),
+        "mean_robustness": float(rho.mean()),
+        "mean_phi_del": float(phid.mean()),
+        "mean_other_fraction": float(other.mean()),
+        "isolated": int(((neutral[:S] + to_del[:S])[d] == N * hist[:S][d]).sum()),
+        "checks": {
+            "sum_designability_is_2^N": total == (1 << N),
+            "neutral_counts_even": bool((neutral % 2 == 0).all()),
+            "minus1_row_consistent": int(neutral[S]) == int(to_del[S]),
+            "flips_other_nonnegative": flips_other >= 0,
+        },
+    }
+
+
+def run_stream(args):
+    """The whole space of a box through the shard streamer (hp_stream_shards)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2008_05612_gb300 as hp
+
+    parts = args.stream.split(":")
+    dims = tuple(int(x) for x in parts[0].split("x"))
+    bits = int(parts[1])
+    window = int(parts[2]) if len(parts) > 2 and parts[2] else None
+    out_dir = parts[3] if len(parts) > 3 else None
+    s = hp.Structs(dims)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist, neutral, to_del, computed = hp.stream_shards(s, bits, window=window, out_dir=out_dir)
+    dt = time.perf_counter() - t0
+    evals = (1 << s.N) * s.S_dir
+    line = {"case": f"stream {args.stream}", "box": parts[0], "N": s.N, "S": s.S, "S_dir": s.S_dir,
+            "shards": 1 << bits, "maps_computed": computed, "seconds": dt,
+            "evals_per_s": evals / dt if computed == (1 << bits) else None,
+            "statistics": map_statistics(hist, neutral, to_del, s.N, s.S)}
+    print(json.dumps(line))
+    return 0
+
+
 def run_map_only(args):
     """Phenotype map of one aligned id block, W + K launches, CUDA-event timed (a small case for ncu)."""
     import torch
@@ -303,6 +362,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (one JSON line)")
+    ap.add_argument("--stream", default=None, metavar="BOX:BITS[:WINDOW[:DIR]]",
+                    help="whole-space map of BOX in 2^BITS shards with exact designability and Eq. 2 statistics")
     ap.add_argument("--proposal-case", action="store_true",
                     help="profiling case: top-4 proposals of an untrained 3x3x3 network for 65,536 ids, W + K times")
     ap.add_argument("--map-only", default=None, metavar="BOX:BITS",
@@ -312,6 +373,8 @@ def main():
         return run_reference(args)
     if args.map_only:
         return run_map_only(args)
+    if args.stream:
+        return run_stream(args)
 
     import torch
 

@@ -229,6 +229,36 @@ int hp_designability_noalloc(const int32_t* d_phen, uint64_t count, int32_t S, u
 int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64_t* d_neutral, uint64_t* d_to_del,
                   void* stream);
 
+/* One row of Eq. 2 over a FULL map of 2^N sequences: for phenotype q (-1
+ * allowed) d_row[p] = sum over g with P(g) = q of #{i : P(g xor 2^i) = p},
+ * index S for -1; phi_pq = d_row[p] / (N * N_q).  This is the neighbourhood
+ * of the top fold analysed in Section 3.2 (Figure 7).
+ *   d_phen: device int32[2^N]; d_row: device uint64[S + 1], overwritten. */
+int hp_neighbourhood(const int32_t* d_phen, int32_t N, int32_t S, int32_t q, uint64_t* d_row, void* stream);
+
+/* Eq. 2 numerators across one high bit between two equally sized aligned
+ * blocks: genotype base_a + x of block A flips to base_b + x of block B.
+ * ADDS to d_neutral[P_A(x)] when P_B(x) = P_A(x) and to d_to_del[P_A(x)]
+ * when P_B(x) = -1 (index S for -1, where both rows count -1 -> -1).
+ * Used by the shard streamer for flips between shards. */
+int hp_robustness_cross(const int32_t* d_phen_a, const int32_t* d_phen_b, uint64_t count, int32_t S,
+                        uint64_t* d_neutral, uint64_t* d_to_del, void* stream);
+
+/* Shard streamer (the paper's 6x6 run of 2^36 genotypes, "underway" in
+ * Sections 3.1 and 4): the full map of a box computed in 2^shard_bits shards
+ * of 2^(N - shard_bits) ids, with designability and the Eq. 2 numerators over
+ * ALL N flip directions accumulated exactly (uint64) into host arrays
+ * h_hist, h_neutral, h_to_del [S + 1] -- equal to hp_designability and
+ * hp_robustness of the full map.  Shard maps live in `window` device buffers
+ * of 4 * 2^(N - shard_bits) bytes (window >= 2^(shard_bits-1) + 1, else
+ * HP_EINVAL before any device work).  out_dir (NULL: none) receives a
+ * manifest and one record per shard and per shard pair, written atomically;
+ * a rerun with the same out_dir reuses every record whose table hash matches
+ * and computes only the shard maps that missing records need (their number
+ * goes to *h_maps_computed if non-NULL).  Synchronises `stream`. */
+int hp_stream_shards(const hp_structs* s, int32_t shard_bits, int32_t window, const char* out_dir, uint64_t* h_hist,
+                     uint64_t* h_neutral, uint64_t* h_to_del, int32_t* h_maps_computed, void* stream);
+
 /* Neutral networks (Section 1; never computed in the paper): connected
  * components of the graph whose vertices are sequences with P(g) != -1 and
  * whose edges join g and g xor 2^i when P is equal.

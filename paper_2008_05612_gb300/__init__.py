@@ -26,7 +26,8 @@ EXPORTS = (
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
     "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
     "hp_batch_plan_free", "hp_sequence_scan", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
-    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neutral_components",
+    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_robustness_cross", "hp_stream_shards",
+    "hp_neutral_components",
     "hp_last_error",
 )
 _VOID = ("hp_structs_free", "hp_last_error", "hp_batch_plan_free", "hp_mlp_free")
@@ -87,6 +88,9 @@ def lib():
         L.hp_designability_noalloc.argtypes = [vp, u64, i32, vp, vp]
         L.hp_robustness.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_neutral_components.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.hp_neighbourhood.argtypes = [vp, i32, i32, i32, vp, vp]
+        L.hp_robustness_cross.argtypes = [vp, vp, u64, i32, vp, vp, vp]
+        L.hp_stream_shards.argtypes = [vp, i32, i32, ctypes.c_char_p, vp, vp, vp, vp, vp]
         L.hp_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in _VOID:
@@ -376,6 +380,45 @@ def robustness(phen, N: int, S: int, stream=None):
     _check(lib().hp_robustness(_dptr(phen, torch.int32, "phen"), N, S, _dptr(neutral, torch.int64, "neutral"),
                                _dptr(to_del, torch.int64, "to_del"), _stream_ptr(stream)))
     return neutral, to_del
+
+
+def neighbourhood(phen, N: int, S: int, q: int, stream=None):
+    """Row q of the Eq. 2 numerators (hp_neighbourhood): int64[S+1], index S for -1."""
+    import torch
+
+    if phen.numel() != (1 << N):
+        raise ValueError("the neighbourhood needs the full map of 2^N sequences")
+    row = torch.empty(S + 1, dtype=torch.int64, device=phen.device)
+    _check(lib().hp_neighbourhood(_dptr(phen, torch.int32, "phen"), N, S, q, _dptr(row, torch.int64, "row"),
+                                  _stream_ptr(stream)))
+    return row
+
+
+def stream_shards(structs: Structs, shard_bits: int, window: int | None = None, out_dir: str | None = None,
+                  stream=None):
+    """hp_stream_shards: (hist, neutral, to_del) numpy uint64 [S+1] over the whole space, and the number of
+    shard maps computed (fewer on a resumed run)."""
+    S = structs.S
+    hist = np.zeros(S + 1, dtype=np.uint64)
+    neutral = np.zeros(S + 1, dtype=np.uint64)
+    to_del = np.zeros(S + 1, dtype=np.uint64)
+    computed = ctypes.c_int32(0)
+    if window is None:
+        window = (1 << (shard_bits - 1)) + 1 if shard_bits > 0 else 1
+    _check(lib().hp_stream_shards(structs.handle, shard_bits, window, out_dir.encode() if out_dir else None,
+                                  hist.ctypes.data_as(ctypes.c_void_p), neutral.ctypes.data_as(ctypes.c_void_p),
+                                  to_del.ctypes.data_as(ctypes.c_void_p), ctypes.byref(computed),
+                                  _stream_ptr(stream) if _cuda_ready() else None))
+    return hist, neutral, to_del, computed.value
+
+
+def _cuda_ready():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except ImportError:
+        return False
 
 
 def neutral_components(phen, N: int, S: int, stream=None):

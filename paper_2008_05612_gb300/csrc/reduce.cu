@@ -421,3 +421,101 @@ extern "C" int hp_designability_noalloc(const int32_t* d_phen, uint64_t count, i
   if (herr & kErrRange) return hp::fail(HP_EINVAL, "hp_designability_noalloc: map entry outside [-1, S)");
   return HP_OK;
 }
+
+// ---------------------------------------------------------------- one row of Eq. 2
+
+namespace {
+
+// out[p] += #{(g, i) : P(g) = q, P(g xor 2^i) = p} over a full 2^N map (index S for -1).  The
+// row is sparse (a phenotype's neighbours are few), so it is accumulated with global atomics
+// issued only by genotypes of phenotype q.
+__global__ void neighbourhood_row(const int32_t* __restrict__ phen, int N, int S, int32_t q,
+                                  unsigned long long* __restrict__ out, unsigned* __restrict__ err) {
+  const unsigned long long total = 1ull << N;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    if (__ldcs(phen + g) != q) continue;
+    for (int i = 0; i < N; i++) {
+      const int32_t p = __ldg(phen + (g ^ (1ull << i)));
+      if (p < -1 || p >= S) {
+        atomicOr(err, kErrRange);
+        continue;
+      }
+      atomicAdd(&out[p < 0 ? S : p], 1ull);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" int hp_neighbourhood(const int32_t* d_phen, int32_t N, int32_t S, int32_t q, uint64_t* d_row, void* stream) {
+  if (!d_phen || !d_row) return hp::fail(HP_EINVAL, "hp_neighbourhood: NULL pointer");
+  if (N < 1 || N > 40) return hp::fail(HP_EINVAL, "hp_neighbourhood: N must be in [1, 40]");
+  if (S < 1 || q < -1 || q >= S) return hp::fail(HP_EINVAL, "hp_neighbourhood: q must be in [-1, S)");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&err, sizeof(unsigned), st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_neighbourhood: cudaMallocAsync");
+  cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(d_row, 0, sizeof(uint64_t) * (size_t)(S + 1), st);
+  const unsigned long long total = 1ull << N;
+  const unsigned grid = (unsigned)std::min<unsigned long long>((total + 255) / 256, (unsigned long long)sm_count() * 16);
+  neighbourhood_row<<<grid, 256, 0, st>>>(d_phen, N, S, q, reinterpret_cast<unsigned long long*>(d_row), err);
+  e = cudaGetLastError();
+  int rc = e == cudaSuccess ? HP_OK : hp::cuda_fail(e, "hp_neighbourhood: launch");
+  return finish_with_err(err, st, "hp_neighbourhood", rc);
+}
+
+// ---------------------------------------------------------------- cross-block flips
+
+namespace {
+
+// Genotypes of block A (ids base_a + x) flipped across one high bit land on base_b + x in block B:
+// neutral[P_A(x)] += [P_B(x) = P_A(x)], to_del[P_A(x)] += [P_B(x) = -1]  (index S for -1).
+__global__ void robustness_cross(const int32_t* __restrict__ a, const int32_t* __restrict__ b, unsigned long long count,
+                                 int S, unsigned long long* __restrict__ neutral, unsigned long long* __restrict__ to_del,
+                                 unsigned* __restrict__ err) {
+  unsigned negneg = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < count; x += stride) {
+    const int32_t pa = __ldcs(a + x), pb = __ldcs(b + x);
+    if (pa < -1 || pa >= S || pb < -1 || pb >= S) {
+      atomicOr(err, kErrRange);
+      continue;
+    }
+    if (pa < 0) {
+      negneg += pb < 0;
+    } else if (pb == pa) {
+      atomicAdd(&neutral[pa], 1ull);
+    } else if (pb < 0) {
+      atomicAdd(&to_del[pa], 1ull);
+    }
+  }
+  for (int off = 16; off; off >>= 1) negneg += __shfl_xor_sync(0xFFFFFFFFu, negneg, off);
+  if ((threadIdx.x & 31) == 0 && negneg) {
+    atomicAdd(&neutral[S], (unsigned long long)negneg);
+    atomicAdd(&to_del[S], (unsigned long long)negneg);
+  }
+}
+
+}  // namespace
+
+extern "C" int hp_robustness_cross(const int32_t* d_phen_a, const int32_t* d_phen_b, uint64_t count, int32_t S,
+                                   uint64_t* d_neutral, uint64_t* d_to_del, void* stream) {
+  if (!d_phen_a || !d_phen_b || !d_neutral || !d_to_del) return hp::fail(HP_EINVAL, "hp_robustness_cross: NULL pointer");
+  if (S < 1) return hp::fail(HP_EINVAL, "hp_robustness_cross: S must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* err = nullptr;
+  cudaError_t e = cudaMallocAsync(&err, sizeof(unsigned), st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_robustness_cross: cudaMallocAsync");
+  cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+  int rc = HP_OK;
+  if (count) {
+    const unsigned grid = (unsigned)std::min<unsigned long long>((count + 255) / 256, (unsigned long long)sm_count() * 16);
+    robustness_cross<<<grid, 256, 0, st>>>(d_phen_a, d_phen_b, count, S, reinterpret_cast<unsigned long long*>(d_neutral),
+                                            reinterpret_cast<unsigned long long*>(d_to_del), err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_robustness_cross: launch");
+  }
+  return finish_with_err(err, st, "hp_robustness_cross", rc);
+}

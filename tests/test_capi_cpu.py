@@ -74,3 +74,12 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text and "hp_oracle" not in text, f
+
+
+def test_stream_shards_rejects_a_small_window_before_device_work():
+    s = hp.Structs((4, 4))
+    with pytest.raises(hp.HPError) as e:
+        hp.stream_shards(s, 3, window=4)
+    assert e.value.code == hp.HP_EINVAL and "window" in str(e.value)
+    with pytest.raises(hp.HPError):
+        hp.stream_shards(s, 16)

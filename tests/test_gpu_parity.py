@@ -179,9 +179,10 @@ def test_paper_statistics_3x3x3(hp):
         "rho_gt_mean_rho": float((rho > rho.mean()).mean()),
     }
     top = int(np.argmax(hist[:S]))
-    members = torch.nonzero(phen == top).flatten()
-    nb = torch.cat([phen[members ^ (1 << i)] for i in range(N)])
-    adj = torch.unique(nb[(nb >= 0) & (nb != top)]).numel()
+    row = hp.neighbourhood(phen, N, S, top).cpu().numpy()
+    assert int(row.sum()) == N * int(hist[top])
+    assert int(row[top]) == int(neutral[top]) and int(row[S]) == int(to_del[top])
+    adj = int((row[:S] > 0).sum()) - 1  # phenotypes other than the top fold reached by one flip
     cand["top_fold_adjacent_of_designable"] = adj / float(d.sum())
     cand["top_fold_adjacent_of_all"] = adj / float(S)
     cand["top_fold_adjacent_count"] = adj
@@ -214,6 +215,16 @@ def synthetic_map(N, S, seed):
     hole = inputs.splitmix64(g ^ np.uint64(seed * 7 + 1)) % np.uint64(4) == 0
     p[hole] = -1
     return p
+
+
+@pytest.mark.parametrize("dims", [(4, 4), (4, 5)])
+def test_neighbourhood_rows_match_oracle(hp, obox, dims):
+    s, phen, _ = gpu_full_map(hp, dims)
+    want = obox(dims).full_map()
+    hist = oracle.designability(want, s.S)
+    for q in [int(np.argmax(hist[: s.S])), int(np.argmin(np.where(hist[: s.S] > 0, hist[: s.S], 1 << 40))), -1]:
+        np.testing.assert_array_equal(hp.neighbourhood(phen, s.N, s.S, q).cpu().numpy().astype(np.uint64),
+                                      oracle.neighbourhood(want, s.N, s.S, q))
 
 
 @pytest.mark.parametrize("N,S,seed", [(12, 5, 1), (20, 300, 2), (24, 51704, 3)])
