@@ -341,6 +341,7 @@ def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 
 
         out, ms = timed(learned)
         _, ms_prop = timed(lambda: hp.proposal_conformations(s, model.topk(ev, k)))
+        model.status()
         exact = int(cnt[0]) / 4  # four calls accumulated (warm-up + 3 timed)
         res[name] = {"ms": ms, "ms_proposal": ms_prop, "sequences_per_s": eval_n / (ms * 1e-3),
                      "exact_eval_fraction": exact / (eval_n * s.S_dir),
@@ -411,7 +412,10 @@ def main():
             net.topk(ev, 4)
         e1.record()
         torch.cuda.synchronize()
-        print(json.dumps({"case": "proposal top-4, 65536 ids", "ms": e0.elapsed_time(e1) / args.steps}))
+        net.status()
+        ms = e0.elapsed_time(e1) / args.steps
+        flops = 2.0 * ev.numel() * (N * 512 + 512 * 512 + 512 * S)
+        print(json.dumps({"case": "proposal top-4, 65536 ids", "ms": ms, "gemm_tflops_equiv": flops / (ms * 1e-3) / 1e12}))
         return 0
     nseq = 1 << N
     stream = torch.cuda.current_stream()

@@ -159,7 +159,9 @@ int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, cons
  * sequence id (1 = H) and proposes likely ground-state classes; their
  * conformations seed the exact bound pruning of hp_sequence_scan.  It never
  * decides a phenotype.  Weights are fp32 masters with bf16 copies; every
- * matrix product is a bf16 tensor-core GEMM with fp32 accumulation; training
+ * matrix product is a bf16 tensor-core GEMM with fp32 accumulation (tcgen05
+ * with a tensor-memory accumulator where the contraction length is a multiple
+ * of 64, else mma.sync); training
  * minimises the mean cross-entropy with Adam (beta 0.9 / 0.999, eps 1e-8). */
 typedef struct hp_mlp hp_mlp;
 
@@ -189,6 +191,16 @@ int hp_mlp_logits(hp_mlp* m, const uint64_t* d_ids, int32_t n, float* d_logits, 
 /* The k (1..16) highest-scoring classes of each of n ids (ties toward the
  * lower class), into device int32[n x k]; runs in chunks of max_batch. */
 int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t k, int32_t* d_top, void* stream);
+
+/* Drain `stream` and report whether any GEMM of this network since the last
+ * check timed out: the tcgen05 GEMM waits on its shared-memory mbarriers with
+ * an iteration limit and, when one runs out, records it in a device word of
+ * the network and skips its output tile.  Returns HP_OK, HP_ETIMEOUT (results
+ * since the last check are invalid; the word is cleared) or HP_ECUDA.
+ * hp_mlp_gradients and hp_mlp_train_step check it themselves whenever they
+ * synchronise; hp_mlp_logits and hp_mlp_topk are asynchronous and leave it to
+ * this call. */
+int hp_mlp_status(hp_mlp* m, void* stream);
 
 /* Expand classes (device int32[n x k], -1 allowed) into their conformations:
  * d_cand[n x 2k], entry 2j + q = q-th conformation of class j or -1. */

@@ -26,7 +26,7 @@ EXPORTS = (
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
     "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
     "hp_batch_plan_free", "hp_sequence_scan", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
-    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_robustness_cross", "hp_stream_shards",
+    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_robustness_cross", "hp_stream_shards",
     "hp_neutral_components",
     "hp_last_error",
 )
@@ -81,6 +81,7 @@ def lib():
         L.hp_mlp_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp, vp]
         L.hp_mlp_logits.argtypes = [vp, vp, i32, vp, vp]
         L.hp_mlp_topk.argtypes = [vp, vp, ctypes.c_int64, i32, vp, vp]
+        L.hp_mlp_status.argtypes = [vp, vp]
         L.hp_proposal_conformations.argtypes = [vp, vp, ctypes.c_int64, i32, vp, vp]
         L.hp_batch_plan_free.argtypes = [vp]
         L.hp_batch_plan_free.restype = None
@@ -336,6 +337,10 @@ class MLP:
         _check(lib().hp_mlp_topk(self._h, ctypes.c_void_p(ids.data_ptr()), ids.numel(), k, _dptr(out, torch.int32, "out"),
                                  _stream_ptr(stream)))
         return out
+
+    def status(self, stream=None):
+        """Drain the stream; raise HPError if a GEMM's bounded wait gave up since the last check."""
+        _check(lib().hp_mlp_status(self._h, _stream_ptr(stream)))
 
 
 def proposal_conformations(structs: Structs, top, stream=None):

@@ -13,11 +13,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "hp_internal.h"
+#include "tc_gemm.h"
 
 namespace {
 
@@ -355,13 +357,13 @@ __global__ void topk_warp(const float* __restrict__ Z, int ldz, int S, int k, in
   }
   for (int c = lane; c < S; c += 32) {
     const float v = __ldcs(z + c);
-    if (v > bv[KT - 1]) {  // equal values arrive in increasing index per lane: keep the earlier one
+    if (v > bv[KT - 1]) {  // equal values arrive in increasing index per lane: the later one never enters
       // insertion into the sorted list (unrolled, branch-free moves)
       float cv = v;
       int ci = c;
 #pragma unroll
       for (int j = 0; j < KT; j++) {
-        const bool take = cv > bv[j];
+        const bool take = cv > bv[j] || (cv == bv[j] && ci < bi[j]);
         const float tv = bv[j];
         const int ti = bi[j];
         bv[j] = take ? cv : bv[j];
@@ -435,15 +437,38 @@ struct hp_mlp {
   float *Z = nullptr, *dHf = nullptr, *loss = nullptr;
   bf16 *dZ = nullptr, *dZT = nullptr, *dA2 = nullptr, *dA2T = nullptr, *dA1 = nullptr, *dA1T = nullptr;
   int32_t* labels = nullptr;
+  unsigned* tc_err = nullptr;  // set by a tcgen05 GEMM whose bounded mbarrier wait gave up
+  // fused top-k: per row up to 16 candidates of each of up to 2 lists per 256-class tile
+  float* cand_v = nullptr;
+  int32_t* cand_i = nullptr;
   int steps = 0;
 };
 
 namespace {
 
+// every GEMM runs on the tcgen05 kernel unless HP_MLP_LEGACY_MMA=1 selects the mma.sync kernels
+bool tc_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HP_MLP_LEGACY_MMA");
+    return !(e && e[0] == '1');
+  }();
+  return on;
+}
+
 int gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const float* bias, int relu, float* Cf,
-         int ldcf, bf16* Cb, int ldcb, cudaStream_t st) {
+         int ldcf, bf16* Cb, int ldcb, cudaStream_t st, unsigned* err) {
   if (K % BK != 0 || lda % 8 != 0 || ldb % 8 != 0) return hp::fail(HP_EINVAL, "gemm: K must be a multiple of 32");
   Gemm g{A, B, lda, ldb, M, N, K, bias, relu, Cf, ldcf, Cb, ldcb};
+  if (tc_enabled()) {
+    hp::TcEpilogue ep;
+    ep.bias = bias;
+    ep.relu = relu;
+    ep.Cf = Cf;
+    ep.ldcf = ldcf;
+    ep.Cb = Cb;
+    ep.ldcb = ldcb;
+    return hp::tc_gemm(A, lda, B, ldb, M, N, K, ep, err, st);
+  }
   using Big = BigGemm<128, 256, 3>;
   if (K % Big::BK == 0 && (long long)M * N >= (1ll << 22) && K >= 128) {
     cudaFuncSetAttribute(gemm_tn_big<128, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Big::kSmemBytes);
@@ -463,16 +488,26 @@ void transpose(const bf16* in, int ldin, int rows, int cols, bf16* out, int ldou
 
 int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
-// Forward pass for rows [0, rows) whose ids are in `ids` (n valid): logits -> m->Z
-void forward(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
+// Hidden layers for rows [0, rows) whose ids are in `ids` (n valid) -> m->Hb2
+int forward_hidden(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
   encode_bits<<<(rows + 7) / 8, dim3(32, 8), 0, st>>>(ids, n, rows, m->N, m->Kin, m->X);
-  gemm(m->X, m->Kin, m->w1b, m->Kin, rows, m->H1, m->Kin, m->w[1], 1, nullptr, 0, m->Hb1, m->H1, st);
-  gemm(m->Hb1, m->H1, m->w2b, m->H1, rows, m->H2, m->H1, m->w[3], 1, nullptr, 0, m->Hb2, m->H2, st);
-  gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, m->w[5], 0, m->Z, m->Spad, nullptr, 0, st);
+  int rc = gemm(m->X, m->Kin, m->w1b, m->Kin, rows, m->H1, m->Kin, m->w[1], 1, nullptr, 0, m->Hb1, m->H1, st, m->tc_err);
+  if (rc == HP_OK)
+    rc = gemm(m->Hb1, m->H1, m->w2b, m->H1, rows, m->H2, m->H1, m->w[3], 1, nullptr, 0, m->Hb2, m->H2, st, m->tc_err);
+  return rc;
+}
+
+// Forward pass: logits -> m->Z
+int forward(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
+  int rc = forward_hidden(m, ids, n, rows, st);
+  if (rc == HP_OK)
+    rc = gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, m->w[5], 0, m->Z, m->Spad, nullptr, 0, st, m->tc_err);
+  return rc;
 }
 
 // Gradients of the mean cross-entropy over the n valid rows into m->g[*]; loss sum into m->loss
-void backward(hp_mlp* m, int n, int rows, cudaStream_t st) {
+int backward(hp_mlp* m, int n, int rows, cudaStream_t st) {
+  int rc = HP_OK;
   const int S = m->S, H1 = m->H1, H2 = m->H2, Kin = m->Kin, Spad = m->Spad;
   cudaMemsetAsync(m->loss, 0, sizeof(float), st);
   softmax_xent<<<rows, 256, 0, st>>>(m->Z, Spad, S, m->labels, m->dZ, Spad, Spad, 1.f / (float)std::max(n, 1), m->loss);
@@ -480,21 +515,22 @@ void backward(hp_mlp* m, int n, int rows, cudaStream_t st) {
   colsum_bf16<<<(S + 255) / 256, 256, 0, st>>>(m->dZ, Spad, rows, S, m->g[5]);
   transpose(m->dZ, Spad, rows, Spad, m->dZT, rows, rows, st);
   transpose(m->Hb2, H2, rows, H2, m->H2T, rows, rows, st);
-  gemm(m->dZT, rows, m->H2T, rows, S, H2, rows, nullptr, 0, m->g[4], H2, nullptr, 0, st);
-  gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, nullptr, 0, m->dHf, H2, nullptr, 0, st);
+  if (rc == HP_OK) rc = gemm(m->dZT, rows, m->H2T, rows, S, H2, rows, nullptr, 0, m->g[4], H2, nullptr, 0, st, m->tc_err);
+  if (rc == HP_OK) rc = gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, nullptr, 0, m->dHf, H2, nullptr, 0, st, m->tc_err);
   relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->dHf, m->Hb2, m->dA2, (size_t)rows * H2);
   // layer 2
   colsum_bf16<<<(H2 + 255) / 256, 256, 0, st>>>(m->dA2, H2, rows, H2, m->g[3]);
   transpose(m->dA2, H2, rows, H2, m->dA2T, rows, rows, st);
   transpose(m->Hb1, H1, rows, H1, m->H1T, rows, rows, st);
-  gemm(m->dA2T, rows, m->H1T, rows, H2, H1, rows, nullptr, 0, m->g[2], H1, nullptr, 0, st);
-  gemm(m->dA2, H2, m->w2t, H2, rows, H1, H2, nullptr, 0, m->dHf, H1, nullptr, 0, st);
+  if (rc == HP_OK) rc = gemm(m->dA2T, rows, m->H1T, rows, H2, H1, rows, nullptr, 0, m->g[2], H1, nullptr, 0, st, m->tc_err);
+  if (rc == HP_OK) rc = gemm(m->dA2, H2, m->w2t, H2, rows, H1, H2, nullptr, 0, m->dHf, H1, nullptr, 0, st, m->tc_err);
   relu_backward<<<grid_for((size_t)rows * H1), 256, 0, st>>>(m->dHf, m->Hb1, m->dA1, (size_t)rows * H1);
   // layer 1
   colsum_bf16<<<(H1 + 255) / 256, 256, 0, st>>>(m->dA1, H1, rows, H1, m->g[1]);
   transpose(m->dA1, H1, rows, H1, m->dA1T, rows, rows, st);
   transpose(m->X, Kin, rows, Kin, m->XT, rows, rows, st);
-  gemm(m->dA1T, rows, m->XT, rows, H1, Kin, rows, nullptr, 0, m->g[0], Kin, nullptr, 0, st);
+  if (rc == HP_OK) rc = gemm(m->dA1T, rows, m->XT, rows, H1, Kin, rows, nullptr, 0, m->g[0], Kin, nullptr, 0, st, m->tc_err);
+  return rc;
 }
 
 // refresh the bf16 copies and transposes used by the forward and backward GEMMs
@@ -514,8 +550,8 @@ void free_model(hp_mlp* m) {
     cudaFree(m->m[i]);
     cudaFree(m->v[i]);
   }
-  void* ptrs[] = {m->w1b, m->w2b, m->w3b, m->w2t, m->w3t, m->X, m->XT, m->Hb1, m->Hb2, m->H1T, m->H2T, m->Z, m->dHf,
-                  m->loss, m->dZ, m->dZT, m->dA2, m->dA2T, m->dA1, m->dA1T, m->labels};
+  void* ptrs[] = {m->w1b, m->w2b, m->w3b, m->w2t, m->w3t, m->X,  m->XT,  m->Hb1, m->Hb2,  m->H1T,  m->H2T,
+                  m->Z,   m->dHf, m->loss, m->dZ,  m->dZT, m->dA2, m->dA2T, m->dA1, m->dA1T, m->labels, m->tc_err, m->cand_v, m->cand_i};
   for (void* p : ptrs) cudaFree(p);
   delete m;
 }
@@ -580,6 +616,10 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
   al(&m->dA1, B * H1 * 2);
   al(&m->dA1T, (size_t)H1 * B * 2);
   al(&m->labels, B * 4);
+  al(&m->tc_err, sizeof(unsigned));
+  const size_t ncand = (size_t)max_batch * ((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcListsPerTile * 16;
+  al(&m->cand_v, ncand * 4);
+  al(&m->cand_i, ncand * 4);
   if (e != cudaSuccess) {
     free_model(m);
     return hp::cuda_fail(e, "hp_mlp_create: device allocation");
@@ -606,6 +646,25 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
 
 extern "C" void hp_mlp_free(hp_mlp* m) { free_model(m); }
 
+namespace {
+// read (and clear) the tcgen05 timeout word after the stream has drained
+int take_status(hp_mlp* m, cudaStream_t st, const char* what) {
+  unsigned flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, m->tc_err, sizeof(flag), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && flag) e = cudaMemsetAsync(m->tc_err, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hp::cuda_fail(e, what);
+  if (flag) return hp::fail(HP_ETIMEOUT, "tcgen05 GEMM: bounded mbarrier wait gave up (results invalid)");
+  return HP_OK;
+}
+}  // namespace
+
+extern "C" int hp_mlp_status(hp_mlp* m, void* stream) {
+  if (!m) return hp::fail(HP_EINVAL, "hp_mlp_status: NULL model");
+  return take_status(m, (cudaStream_t)stream, "hp_mlp_status");
+}
+
 extern "C" int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t* d_labels, int32_t n,
                                  float* const* h_grads, float* h_loss, void* stream) {
   if (!m || !d_ids || !d_labels) return hp::fail(HP_EINVAL, "hp_mlp_gradients: NULL argument");
@@ -614,8 +673,9 @@ extern "C" int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t*
   const int rows = round_up(n, 32);
   cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
   cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-  forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
-  backward(m, n, rows, st);
+  int rc = forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
+  if (rc == HP_OK) rc = backward(m, n, rows, st);
+  if (rc != HP_OK) return rc;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_gradients: launch");
   if (h_grads) {
@@ -635,6 +695,7 @@ extern "C" int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t*
     *h_loss = l / (float)n;
   }
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_gradients");
+  if (h_grads || h_loss) return take_status(m, st, "hp_mlp_gradients");
   return HP_OK;
 }
 
@@ -646,8 +707,9 @@ extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t
   const int rows = round_up(n, 32);
   cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
   cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-  forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
-  backward(m, n, rows, st);
+  int rc = forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
+  if (rc == HP_OK) rc = backward(m, n, rows, st);
+  if (rc != HP_OK) return rc;
   m->steps++;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = 1.f / (1.f - powf(b1, (float)m->steps)), c2 = 1.f / (1.f - powf(b2, (float)m->steps));
@@ -663,6 +725,7 @@ extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_train_step");
     *h_loss = l / (float)n;
+    return take_status(m, st, "hp_mlp_train_step");
   }
   return HP_OK;
 }
@@ -674,8 +737,23 @@ extern "C" int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t 
   for (int64_t off = 0; off < n; off += m->max_batch) {
     const int nb = (int)std::min<int64_t>(m->max_batch, n - off);
     const int rows = round_up(nb, 32);
-    forward(m, reinterpret_cast<const unsigned long long*>(d_ids) + off, nb, rows, st);
-    launch_topk(m->Z, m->Spad, m->S, k, nb, d_top + off * k, st);
+    const unsigned long long* ids = reinterpret_cast<const unsigned long long*>(d_ids) + off;
+    if (tc_enabled()) {
+      // output layer with the top-k fused into the GEMM epilogue: logits never reach memory
+      int rc = forward_hidden(m, ids, nb, rows, st);
+      hp::TcEpilogue ep;
+      ep.bias = m->w[5];
+      ep.kt = k <= 4 ? 4 : k <= 8 ? 8 : 16;
+      ep.cand_v = m->cand_v;
+      ep.cand_i = m->cand_i;
+      if (rc == HP_OK) rc = hp::tc_gemm(m->Hb2, m->H2, m->w3b, m->H2, nb, m->S, m->H2, ep, m->tc_err, st);
+      if (rc != HP_OK) return rc;
+      hp::tc_topk_merge(m->cand_v, m->cand_i, hp::tc_topk_lists(nb, m->S), nb, ep.kt, k, m->S, d_top + off * k, st);
+    } else {
+      int rc = forward(m, ids, nb, rows, st);
+      if (rc != HP_OK) return rc;
+      launch_topk(m->Z, m->Spad, m->S, k, nb, d_top + off * k, st);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_topk: launch");
@@ -685,7 +763,8 @@ extern "C" int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t 
 extern "C" int hp_mlp_logits(hp_mlp* m, const uint64_t* d_ids, int32_t n, float* d_logits, void* stream) {
   if (!m || !d_ids || !d_logits || n < 1 || n > m->max_batch) return hp::fail(HP_EINVAL, "hp_mlp_logits: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
-  forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, round_up(n, 32), st);
+  const int rc = forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, round_up(n, 32), st);
+  if (rc != HP_OK) return rc;
   cudaError_t e = cudaMemcpy2DAsync(d_logits, (size_t)m->S * 4, m->Z, (size_t)m->Spad * 4, (size_t)m->S * 4, n,
                                     cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_logits");

@@ -52,6 +52,7 @@ def test_logits_match_fp64_reference(hp, N, H1, H2, S, n):
     net = hp.MLP(N, H1, H2, S, 512, p)
     ids = inputs.sample_ids(N, n, seed=3)
     got = net.logits(ids_tensor(ids)).cpu().numpy().astype(np.float64)
+    net.status()  # no tcgen05 wait gave up
     x = omlp.bits(ids, N)
     # reference with the bf16 roundings the GPU applies to operands and hidden activations
     W1, b1, W2, b2, W3, b3 = p
@@ -63,9 +64,10 @@ def test_logits_match_fp64_reference(hp, N, H1, H2, S, n):
     assert rel(got, omlp.forward(p, x)[4]) < TOL
 
 
-@pytest.mark.parametrize("N,H1,H2,S,n", [(27, 64, 64, 200, 96), (27, 512, 512, 8200, 512)])
+@pytest.mark.parametrize("N,H1,H2,S,n", [(27, 64, 64, 200, 96), (36, 128, 192, 1000, 250), (27, 512, 512, 8200, 512)])
 def test_gradients_match_oracle(hp, N, H1, H2, S, n):
-    """The second shape routes the output layer and its gradients through the large-tile GEMM."""
+    """Forward and backward GEMMs with K % 64 == 0 run on the tcgen05 kernel (ragged M and N tiles in the
+    second shape, eight K chunks in the third); the rest on mma.sync."""
     p = init(N, H1, H2, S, 21)
     net = hp.MLP(N, H1, H2, S, max(128, n), p)
     ids = inputs.sample_ids(N, n, seed=8)
@@ -107,6 +109,24 @@ def test_topk_matches_sorted_logits(hp):
     z = net.logits(ids).cpu().numpy()
     top = net.topk(ids, 5).cpu().numpy()
     want = np.argsort(-z, axis=1, kind="stable")[:, :5]
+    np.testing.assert_array_equal(top, want)
+
+
+@pytest.mark.parametrize("k", [1, 4, 7, 16])
+def test_topk_ties_tiles_and_chunks(hp, k):
+    """Fused top-k (per 256-class tile, then merged) against a stable sort of the logits: classes
+    repeat every 97 rows of W3 (many exact ties, resolved toward the lower class), S = 1291 leaves an
+    11-class last tile (fewer than k = 16 candidates), and 700 ids run in chunks of 256."""
+    N, H1, H2, S = 27, 64, 128, 1291
+    W1, b1, W2, b2, W3, b3 = init(N, H1, H2, S, 43)
+    W3 = W3[np.arange(S) % 97].copy()
+    b3 = b3[np.arange(S) % 97].copy()
+    net = hp.MLP(N, H1, H2, S, 256, [W1, b1, W2, b2, W3, b3])
+    ids = ids_tensor(inputs.sample_ids(N, 700, seed=6))
+    z = np.concatenate([net.logits(ids[i:i + 256]).cpu().numpy() for i in range(0, 700, 256)])
+    top = net.topk(ids, k).cpu().numpy()
+    net.status()
+    want = np.argsort(-z, axis=1, kind="stable")[:, :k]
     np.testing.assert_array_equal(top, want)
 
 
