@@ -4,10 +4,13 @@
 // The paper has no learned component; this only ever proposes candidates, it
 // never decides a phenotype.
 //
-// Kernels (all hand-written): a bf16 tensor-core GEMM C = A B^T with fp32
-// accumulation (mma.sync m16n8k16, ldmatrix, cp.async double buffering,
-// fused bias / ReLU epilogue), tiled bf16 transposes, softmax cross-entropy,
-// column sums, ReLU backward, Adam, id -> bit encoding and per-row top-k.
+// Kernels (all hand-written): the GEMMs C = A B^T run on the tcgen05 kernel of
+// tc_gemm.cu (the output layer of the proposal with its top-k fused into the
+// epilogue); the earlier mma.sync m16n8k16 kernels (ldmatrix, cp.async double
+// buffering, fused bias / ReLU epilogue) stay as a comparison path selected by
+// HP_MLP_LEGACY_MMA=1.  Also here: tiled bf16 transposes, softmax
+// cross-entropy, column sums, ReLU backward, Adam, id -> bit encoding and the
+// per-row top-k of the comparison path.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
