@@ -80,7 +80,7 @@ extern "C" void hp_structs_free(hp_structs* s) {
     if (cudaSetDevice(t->device) == cudaSuccess) {
       cudaFree(t->rec);
       cudaFree(t->conf_class);
-      if (t->scan_rec) cudaFree(t->scan_rec);
+      if (t->scan_soa) cudaFree(t->scan_soa);
       if (t->scan_idx) cudaFree(t->scan_idx);
       if (t->scan_tb) cudaFree(t->scan_tb);
       if (t->class_first) cudaFree(t->class_first);

@@ -26,7 +26,7 @@ struct DevTables {
   // per-sequence scan tables (built on first use): records in scan order (conformations
   // sorted by their contact-count vectors so that a tile's bound is tight), the original
   // index of each, and per-tile bound masks
-  uint32_t* scan_rec = nullptr;  // S_pad x rec_words
+  uint32_t* scan_soa = nullptr;  // per 128-conformation tile: (6 + NE) words x 128, word-major
   int32_t* scan_idx = nullptr;   // S_pad (-1 for padding)
   uint32_t* scan_tb = nullptr;   // ntiles x 8 words
   int scan_tile = 0;
