@@ -346,7 +346,7 @@ def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 
         bounds = int(cnt[1]) / 4
         res[name] = {"ms": ms, "ms_proposal": ms_prop, "sequences_per_s": eval_n / (ms * 1e-3),
                      "exact_eval_fraction": exact / (eval_n * s.S_dir),
-                     "bound_eval_fraction": bounds / (eval_n * s.S_dir),
+                     "group_bounds_per_sequence": bounds / eval_n,
                      "mismatches_vs_plain": int((out != plain).sum().item())}
     return {
         "box": "3x3x3", "train_ids": int(tids.numel()), "train_steps": steps, "batch": batch, "lr": lr,

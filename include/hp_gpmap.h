@@ -138,17 +138,18 @@ void hp_batch_plan_free(hp_batch_plan* plan);
  * the paper's sampling mode of Table 3), one warp per sequence, with optional
  * exact bound pruning seeded by candidate conformations (the learned
  * proposal).  With A_s(h) = sum_i h_i c_i(s) and B the HH-contact count,
- * -E = 10 A + 3 B <= 10 A + 3 min(C, floor(A/2)) (Eq. 1, Table 1 x 10); a
- * conformation (or a whole tile of them, using per-tile maximum contact counts)
- * whose bound is below the best exact score among the candidates is skipped.
- * Skips are strict, so results equal the full scan's exactly.
+ * -E = 10 A + 3 B <= 10 A + 3 min(C, floor(A/2)) (Eq. 1, Table 1 x 10); A
+ * depends on a conformation only through its contact-count vector, so the
+ * bound is taken once per group of conformations sharing that vector, and a
+ * group whose bound is below the best exact score among the candidates is
+ * skipped.  Skips are strict, so results equal the full scan's exactly.
  *   d_ids:      device uint64[n] sequence ids (< 2^N);
  *   d_cand:     device int32[n * k] candidate conformation indices (canonical
  *               order, -1 = none) or NULL for the plain full scan;
  *   d_phen:     device int32[n] phenotypes; d_aux: device int32[n] class of
  *               the lowest-index minimum (or NULL);
  *   d_counters: device uint64[2] (or NULL): conformations evaluated exactly
- *               and conformation bounds evaluated are ADDED to [0] and [1].
+ *               and group bounds evaluated are ADDED to [0] and [1].
  * Stream-ordered; does not synchronise.  No counterpart in the paper beyond
  * its sampled kernel (Appendix C). */
 int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand, int32_t k,

@@ -80,9 +80,11 @@ extern "C" void hp_structs_free(hp_structs* s) {
     if (cudaSetDevice(t->device) == cudaSuccess) {
       cudaFree(t->rec);
       cudaFree(t->conf_class);
-      if (t->scan_soa) cudaFree(t->scan_soa);
-      if (t->scan_idx) cudaFree(t->scan_idx);
-      if (t->scan_tb) cudaFree(t->scan_tb);
+      if (t->scan_gcnt) cudaFree(t->scan_gcnt);
+      if (t->scan_gbeg) cudaFree(t->scan_gbeg);
+      if (t->scan_mcnt) cudaFree(t->scan_mcnt);
+      if (t->scan_mmask) cudaFree(t->scan_mmask);
+      if (t->scan_midx) cudaFree(t->scan_midx);
       if (t->class_first) cudaFree(t->class_first);
       if (t->class_nconf) cudaFree(t->class_nconf);
       if (t->half_otab) cudaFree(t->half_otab);

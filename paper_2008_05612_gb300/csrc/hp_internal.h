@@ -23,13 +23,14 @@ struct DevTables {
   int device = -1;
   uint32_t* rec = nullptr;       // S_pad x rec_words contact records
   int32_t* conf_class = nullptr; // S_dir class ids
-  // per-sequence scan tables (built on first use): records in scan order (conformations
-  // sorted by their contact-count vectors so that a tile's bound is tight), the original
-  // index of each, and per-tile bound masks
-  uint32_t* scan_soa = nullptr;  // per 128-conformation tile: (6 + NE) words x 128, word-major
-  int32_t* scan_idx = nullptr;   // S_pad (-1 for padding)
-  uint32_t* scan_tb = nullptr;   // ntiles x 8 words
-  int scan_tile = 0;
+  // per-sequence scan tables (built on first use): conformations sorted by their contact-count
+  // vectors; a group is a run of equal vectors (equal A for every sequence)
+  uint32_t* scan_gcnt = nullptr;   // 6 x gpad: per group the six count bit-planes, word-major
+  int32_t* scan_gbeg = nullptr;    // ngroups + 1: first member of each group (scan order)
+  uint32_t* scan_mcnt = nullptr;   // 6 x spad: per member its count bit-planes, word-major
+  uint32_t* scan_mmask = nullptr;  // NE x spad: per member its contact masks, word-major
+  int32_t* scan_midx = nullptr;    // spad: original conformation index of each member
+  int scan_ngroups = 0, scan_gpad = 0, scan_spad = 0;
   // class -> first conformation index and number of conformations (built on first use)
   int32_t* class_first = nullptr;
   int32_t* class_nconf = nullptr;

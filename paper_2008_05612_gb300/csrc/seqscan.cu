@@ -9,15 +9,20 @@
 // so with a candidate score x_cand (the best exact score among the candidate
 // conformations, a lower bound on the true best) every conformation with
 // U(A_s(h)) < x_cand can neither be the minimum nor tie it and is skipped.
-// The same test on per-tile maxima of the contact counts (conformations sorted
-// by their contact-count vectors, so tiles are homogeneous) skips whole tiles:
-// the lanes test 32 tiles at once and the warp visits the survivors.  Skips are
-// strict, so the phenotype, the tie status and the lowest-index minimiser are
-// exactly those of the full scan.
+// Skips are strict, so the phenotype, the tie status and the lowest-index
+// minimiser are exactly those of the full scan.
 //
-// Tables are word-major inside each 128-conformation tile (the six count
-// bit-planes, then the NE contact masks, each as 128 consecutive words), so
-// the lanes' loads for their four conformations of a tile are coalesced.
+// A depends on a conformation only through its contact-count vector c(s), and
+// many conformations share one (3x3x3: 103,346 conformations, 6,291 vectors).
+// Conformations are therefore sorted by c(s) and scanned group by group (a
+// group = a run of equal vectors): the lanes compute A and the bound for 32
+// groups at once, a warp prefix sum lays the members of the groups that
+// survive end to end, and each lane takes one member per round, finds its
+// group by a shuffle binary search and adds only B (its contact masks of the H
+// even residues).  Without a candidate score there is nothing to prune and
+// the members are scanned directly, two per lane at a time with A from their
+// own count planes.  Tables are word-major (count planes by group and by
+// member, masks by member), so the lanes' loads are coalesced.
 //
 // Reductions use warp primitives: running best / count / first index per lane,
 // then __reduce_max_sync, __reduce_add_sync and __reduce_min_sync.
@@ -34,22 +39,23 @@
 
 namespace {
 
-constexpr int kScanTile = 128;   // conformations per bound tile
-constexpr int kScanWarps = 8;    // warps (sequences in flight) per CTA
+constexpr int kScanWarps = 8;  // warps (sequences in flight) per CTA
 
 struct ScanParams {
-  const uint32_t* soa;       // scan-order tables, (6 + NE) x 128 words per tile
-  const int32_t* idx;        // original index of each scan-order record (-1 padding)
-  const uint32_t* tb;        // per tile: [0..2] even-residue max-count masks, [3..5] odd-residue ones
+  const uint32_t* gcnt;      // 6 x gpad count planes per group (even bits 0..2, odd bits 0..2)
+  const int32_t* gbeg;       // ngroups + 1 member ranges
+  const uint32_t* mcnt;      // 6 x spad count planes per member (the unpruned scan)
+  const uint32_t* mmask;     // NE x spad contact masks per member
+  const int32_t* midx;       // original index per member
   const uint32_t* orig_rec;  // original-order records (candidates)
   const int32_t* conf_class;
   const unsigned long long* ids;
   const int32_t* cand;       // n x k original conformation indices (-1: none) or NULL
   int32_t* phen;
   int32_t* aux;
-  unsigned long long* counters;  // [0] conformations evaluated exactly, [1] bounds evaluated
+  unsigned long long* counters;  // [0] conformations evaluated exactly, [1] group bounds evaluated
   long long n;
-  int k, rec_words, NE, C, S_dir, ntiles, prune;
+  int k, rec_words, NE, C, S_dir, ngroups, gpad, spad, prune;
 };
 
 __device__ __forceinline__ uint32_t even_of(unsigned long long g) {
@@ -72,13 +78,6 @@ __device__ __forceinline__ int weight_sum(uint32_t e, uint32_t o, const uint32_t
 }
 __device__ __forceinline__ int upper(int A, int C) { return 10 * A + 3 * min(C, A >> 1); }
 
-// A of one conformation from its six word-major count planes (c points at its tile slot)
-__device__ __forceinline__ int count_sum(uint32_t e, uint32_t o, const uint32_t* c) {
-  constexpr int T = kScanTile;
-  return (__popc(e & __ldg(c)) + __popc(o & __ldg(c + 3 * T))) + 2 * (__popc(e & __ldg(c + T)) + __popc(o & __ldg(c + 4 * T))) +
-         4 * (__popc(e & __ldg(c + 2 * T)) + __popc(o & __ldg(c + 5 * T)));
-}
-
 // exact score of (e, o) on one record
 __device__ __forceinline__ int score_of(const uint32_t* r, int NE, uint32_t e, uint32_t o, int A) {
   int B = 0;
@@ -89,7 +88,6 @@ __device__ __forceinline__ int score_of(const uint32_t* r, int NE, uint32_t e, u
 __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const ScanParams p) {
   const int lane = threadIdx.x & 31;
   const long long warps_total = (long long)gridDim.x * kScanWarps;
-  const size_t tile_words = (size_t)(6 + p.NE) * kScanTile;
   unsigned long long n_exact = 0, n_bound = 0;
   for (long long q = (long long)blockIdx.x * kScanWarps + (threadIdx.x >> 5); q < p.n; q += warps_total) {
     const unsigned long long g = p.ids[q];
@@ -109,66 +107,86 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
       cand = __reduce_max_sync(0xFFFFFFFFu, best);
     }
     int best = -1, cnt = 0, first = INT_MAX;
-    for (int t0 = 0; t0 < p.ntiles; t0 += 32) {
-      // lane l tests tile t0 + l
-      const int tl = t0 + lane;
-      bool keep = tl < p.ntiles;
-      if (keep && cand >= 0) {
-        const uint32_t* tb = p.tb + (size_t)tl * 8;
-        keep = upper(weight_sum(e, o, tb, tb + 3), p.C) >= cand;
+    auto take = [&](int x, int orig) {
+      n_exact++;
+      if (x > best) {
+        best = x;
+        cnt = 1;
+        first = orig;
+      } else if (x == best) {
+        cnt++;
+        first = min(first, orig);
       }
-      for (uint32_t kept = __ballot_sync(0xFFFFFFFFu, keep); kept; kept &= kept - 1) {
-        const int t = t0 + __ffs(kept) - 1;
-        const uint32_t* base = p.soa + (size_t)t * tile_words;
-        // two conformations per lane at a time; every load of a pair is independent of the
-        // others, so they are all in flight together
+    };
+    if (cand < 0) {
+      // nothing to prune with: every member, two per lane at a time, A from its own count planes
+      for (int m0 = 0; m0 < p.S_dir; m0 += 64) {
+        const int m[2] = {m0 + lane, m0 + 32 + lane};
+        int A[2], B[2] = {0, 0}, orig[2];
 #pragma unroll
-        for (int r = 0; r < kScanTile / 32; r += 2) {
-          const int i0 = lane + 32 * r, i1 = i0 + 32;
-          const int orig0 = __ldg(p.idx + t * kScanTile + i0), orig1 = __ldg(p.idx + t * kScanTile + i1);
-          const uint32_t* c0 = base + i0;
-          const uint32_t* c1 = base + i1;
-          const int A0 = count_sum(e, o, c0), A1 = count_sum(e, o, c1);
-          const bool need0 = orig0 >= 0 && (cand < 0 || upper(A0, p.C) >= cand);
-          const bool need1 = orig1 >= 0 && (cand < 0 || upper(A1, p.C) >= cand);
-          n_bound += (orig0 >= 0) + (orig1 >= 0);
-          if (!__any_sync(0xFFFFFFFFu, need0 || need1)) continue;
-          // B = sum over the H even residues k of #H odd neighbours (mask word 6 + k); e is the
-          // same for the whole warp, so the bit tests are uniform
-          int B0 = 0, B1 = 0;
+        for (int u = 0; u < 2; u++) {
+          const int mm = min(m[u], p.spad - 1);
+          const uint32_t* c = p.mcnt + mm;
+          const size_t w = (size_t)p.spad;
+          A[u] = (__popc(e & __ldg(c)) + __popc(o & __ldg(c + 3 * w))) +
+                 2 * (__popc(e & __ldg(c + w)) + __popc(o & __ldg(c + 4 * w))) +
+                 4 * (__popc(e & __ldg(c + 2 * w)) + __popc(o & __ldg(c + 5 * w)));
+          orig[u] = m[u] < p.S_dir ? __ldg(p.midx + mm) : -1;
+        }
 #pragma unroll
-          for (int k = 0; k < hp::kMaxHalf; k++) {
-            if ((e >> k) & 1u) {
-              const uint32_t w0 = need0 ? __ldg(c0 + (6 + k) * kScanTile) : 0u;
-              const uint32_t w1 = need1 ? __ldg(c1 + (6 + k) * kScanTile) : 0u;
-              B0 += __popc(o & w0);
-              B1 += __popc(o & w1);
-            }
+        for (int k = 0; k < hp::kMaxHalf; k++)
+          if ((e >> k) & 1u) {
+#pragma unroll
+            for (int u = 0; u < 2; u++) B[u] += __popc(o & __ldg(p.mmask + (size_t)k * p.spad + min(m[u], p.spad - 1)));
           }
-          if (need0) {
-            const int x = 10 * A0 + 3 * B0;
-            n_exact++;
-            if (x > best) {
-              best = x;
-              cnt = 1;
-              first = orig0;
-            } else if (x == best) {
-              cnt++;
-              first = min(first, orig0);
-            }
-          }
-          if (need1) {
-            const int x = 10 * A1 + 3 * B1;
-            n_exact++;
-            if (x > best) {
-              best = x;
-              cnt = 1;
-              first = orig1;
-            } else if (x == best) {
-              cnt++;
-              first = min(first, orig1);
-            }
-          }
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+          if (orig[u] >= 0) take(10 * A[u] + 3 * B[u], orig[u]);
+      }
+    }
+    for (int g0 = 0; cand >= 0 && g0 < p.ngroups; g0 += 32) {
+      // lane l: group g0 + l, its A and bound
+      const int gi = g0 + lane;
+      int A = 0, n = 0, beg = 0;
+      if (gi < p.ngroups) {
+        const uint32_t* c = p.gcnt + gi;
+        const size_t w = (size_t)p.gpad;
+        A = (__popc(e & __ldg(c)) + __popc(o & __ldg(c + 3 * w))) + 2 * (__popc(e & __ldg(c + w)) + __popc(o & __ldg(c + 4 * w))) +
+            4 * (__popc(e & __ldg(c + 2 * w)) + __popc(o & __ldg(c + 5 * w)));
+        beg = __ldg(p.gbeg + gi);
+        n_bound++;
+        if (cand < 0 || upper(A, p.C) >= cand) n = __ldg(p.gbeg + gi + 1) - beg;
+      }
+      // inclusive prefix sum of the surviving members over the lanes
+      int incl = n;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+      }
+      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        // the lane L whose range holds idx: the number of lanes with incl <= idx
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const int probe = __shfl_sync(0xFFFFFFFFu, incl, L + step - 1);
+          if (probe <= idx) L += step;
+        }
+        L = min(L, 31);
+        const int gA = __shfl_sync(0xFFFFFFFFu, A, L);
+        const int gbeg = __shfl_sync(0xFFFFFFFFu, beg, L);
+        const int gex = __shfl_sync(0xFFFFFFFFu, incl - n, L);
+        if (idx < total) {
+          const int m = gbeg + (idx - gex);
+          const int orig = __ldg(p.midx + m);
+          // B = sum over the H even residues k of #H odd neighbours; the bit tests are uniform
+          int B = 0;
+#pragma unroll
+          for (int k = 0; k < hp::kMaxHalf; k++)
+            if ((e >> k) & 1u) B += __popc(o & __ldg(p.mmask + (size_t)k * p.spad + m));
+          take(10 * gA + 3 * B, orig);
         }
       }
     }
@@ -198,20 +216,18 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
 namespace hp {
 
 // Scan order: conformations sorted by their vector of per-residue contact
-// counts (lexicographic), so consecutive ones expose similar residues and the
-// per-tile maxima of the counts stay close to each member's counts.
+// counts (lexicographic, stable), so equal vectors form contiguous groups.
 int scan_tables(const hp_structs* cs, DevTables** out) {
   DevTables* dt = nullptr;
   int rc = device_tables(cs, &dt);
   if (rc != HP_OK) return rc;
   hp_structs* s = const_cast<hp_structs*>(cs);
   std::lock_guard<std::mutex> lock(s->mu);
-  if (dt->scan_soa) {
+  if (dt->scan_gcnt) {
     *out = dt;
     return HP_OK;
   }
   const int N = s->N, NE = s->NE, W = s->rec_words;
-  const size_t spad = ((size_t)s->S_dir + kRecPad - 1) / kRecPad * kRecPad;
   std::vector<std::vector<uint8_t>> cvec((size_t)s->S_dir, std::vector<uint8_t>(N, 0));
   for (int32_t c = 0; c < s->S_dir; c++)
     for (int k = 0; k < s->C; k++) {
@@ -221,47 +237,56 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
   std::vector<int32_t> order((size_t)s->S_dir);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cvec[a] < cvec[b]; });
-  // word-major tiles: count planes (even residues bits 0..2 = record words NE+3..NE+5, odd
-  // residues = NE..NE+2), then the NE contact masks (record words 0..NE-1)
-  const int TW = 6 + NE;
-  const int ntiles = (int)(spad / kScanTile);
-  std::vector<uint32_t> soa((size_t)ntiles * TW * kScanTile, 0u);
-  std::vector<int32_t> idx(spad, -1);
+  std::vector<int32_t> gbeg;
+  for (size_t j = 0; j < order.size(); j++)
+    if (j == 0 || cvec[order[j]] != cvec[order[j - 1]]) gbeg.push_back((int32_t)j);
+  const int ngroups = (int)gbeg.size();
+  gbeg.push_back((int32_t)order.size());
+  const int gpad = (ngroups + 31) / 32 * 32, spad = (s->S_dir + 31) / 32 * 32;
+  std::vector<uint32_t> gcnt((size_t)6 * gpad, 0u), mcnt((size_t)6 * spad, 0u), mmask((size_t)std::max(NE, 1) * spad, 0u);
+  std::vector<int32_t> midx(spad, -1);
+  for (int gi = 0; gi < ngroups; gi++) {
+    const uint32_t* r = s->rec.data() + (size_t)order[gbeg[gi]] * W;  // count planes of any member
+    for (int b = 0; b < 3; b++) {
+      gcnt[(size_t)b * gpad + gi] = r[NE + 3 + b];
+      gcnt[(size_t)(3 + b) * gpad + gi] = r[NE + b];
+    }
+  }
   for (size_t j = 0; j < order.size(); j++) {
     const uint32_t* r = s->rec.data() + (size_t)order[j] * W;
-    uint32_t* t = soa.data() + (j / kScanTile) * TW * kScanTile + (j % kScanTile);
+    for (int k = 0; k < NE; k++) mmask[(size_t)k * spad + j] = r[k];
     for (int b = 0; b < 3; b++) {
-      t[(size_t)b * kScanTile] = r[NE + 3 + b];
-      t[(size_t)(3 + b) * kScanTile] = r[NE + b];
+      mcnt[(size_t)b * spad + j] = r[NE + 3 + b];
+      mcnt[(size_t)(3 + b) * spad + j] = r[NE + b];
     }
-    for (int k = 0; k < NE; k++) t[(size_t)(6 + k) * kScanTile] = r[k];
-    idx[j] = order[j];
+    midx[j] = order[j];
   }
-  std::vector<uint32_t> tb((size_t)ntiles * 8, 0u);
-  for (int t = 0; t < ntiles; t++) {
-    uint8_t cmax[kMaxN] = {0};
-    for (int j = t * kScanTile; j < (t + 1) * kScanTile && j < s->S_dir; j++)
-      for (int i = 0; i < N; i++) cmax[i] = std::max(cmax[i], cvec[order[j]][i]);
-    for (int i = 0; i < N; i++)
-      for (int b = 0; b < 3; b++)
-        if ((cmax[i] >> b) & 1) tb[(size_t)t * 8 + ((i & 1) ? 3 : 0) + b] |= 1u << (i / 2);
-  }
-  cudaError_t e = cudaMalloc(&dt->scan_soa, soa.size() * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_idx, idx.size() * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_tb, tb.size() * 4);
-  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_soa, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_tb, tb.data(), tb.size() * 4, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc(&dt->scan_gcnt, gcnt.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_gbeg, gbeg.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_mcnt, mcnt.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_mmask, mmask.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_midx, midx.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_gcnt, gcnt.data(), gcnt.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_gbeg, gbeg.data(), gbeg.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_mcnt, mcnt.data(), mcnt.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_mmask, mmask.data(), mmask.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_midx, midx.data(), midx.size() * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    cudaFree(dt->scan_soa);
-    cudaFree(dt->scan_idx);
-    cudaFree(dt->scan_tb);
-    dt->scan_soa = nullptr;
-    dt->scan_idx = nullptr;
-    dt->scan_tb = nullptr;
+    cudaFree(dt->scan_gcnt);
+    cudaFree(dt->scan_gbeg);
+    cudaFree(dt->scan_mcnt);
+    cudaFree(dt->scan_mmask);
+    cudaFree(dt->scan_midx);
+    dt->scan_mcnt = nullptr;
+    dt->scan_gcnt = nullptr;
+    dt->scan_gbeg = nullptr;
+    dt->scan_mmask = nullptr;
+    dt->scan_midx = nullptr;
     return cuda_fail(e, "per-sequence scan tables");
   }
-  dt->scan_tile = kScanTile;
+  dt->scan_ngroups = ngroups;
+  dt->scan_gpad = gpad;
+  dt->scan_spad = spad;
   *out = dt;
   return HP_OK;
 }
@@ -278,9 +303,11 @@ extern "C" int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int6
   int rc = hp::scan_tables(s, &dt);
   if (rc != HP_OK) return rc;
   ScanParams p;
-  p.soa = dt->scan_soa;
-  p.idx = dt->scan_idx;
-  p.tb = dt->scan_tb;
+  p.gcnt = dt->scan_gcnt;
+  p.gbeg = dt->scan_gbeg;
+  p.mcnt = dt->scan_mcnt;
+  p.mmask = dt->scan_mmask;
+  p.midx = dt->scan_midx;
   p.orig_rec = dt->rec;
   p.conf_class = dt->conf_class;
   p.ids = reinterpret_cast<const unsigned long long*>(d_ids);
@@ -294,7 +321,9 @@ extern "C" int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int6
   p.NE = s->NE;
   p.C = s->C;
   p.S_dir = s->S_dir;
-  p.ntiles = (int)((((size_t)s->S_dir + hp::kRecPad - 1) / hp::kRecPad * hp::kRecPad) / kScanTile);
+  p.ngroups = dt->scan_ngroups;
+  p.gpad = dt->scan_gpad;
+  p.spad = dt->scan_spad;
   p.prune = d_cand != nullptr;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
