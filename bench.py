@@ -274,6 +274,9 @@ def run_map_only(args):
     return 0
 
 
+PROPOSAL_ROWS = 16384  # ids per proposal chunk (the network's max_batch)
+
+
 def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 1 << 16, k: int = 4,
                 batch: int = 4096, lr: float = 1e-3):
     """Learned proposal + bound-pruned scan vs the plain per-sequence scan on the same seeded ids.
@@ -298,8 +301,9 @@ def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 
     params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
               inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
               inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
-    net = hp.MLP(N, 512, 512, S, batch, params)
-    untrained = hp.MLP(N, 512, 512, S, batch, params)
+    # rows per forward chunk: training steps use `batch` of them, the proposal runs 16384 at a time
+    net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
+    untrained = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
     steps = max(1, int(train_fraction_epochs * tids.numel() / batch))
     gen = torch.Generator(device=dev).manual_seed(0)
     perm = torch.randperm(tids.numel(), device=dev, generator=gen)
@@ -403,7 +407,7 @@ def main():
         params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
                   inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
                   inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
-        net = hp.MLP(N, 512, 512, S, 4096, params)
+        net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
         ev = torch.from_numpy(inputs.sample_ids(N, 1 << 16, seed=123).view(np.int64)).cuda()
         for _ in range(args.warmup):
             net.topk(ev, 4)
