@@ -33,7 +33,10 @@
 // staged tile by tile into shared memory with the bulk-copy engine
 // (cp.async.bulk + mbarrier, bounded waits), double buffered; one thread per
 // conformation turns a record into the CTA's coefficient record (lane table,
-// warp table, packed tree coefficients) in a second double buffer.  CTAs are
+// warp table, packed tree coefficients) in a second double buffer; in pass 1 the
+// records of tile t + 1 are produced halfway through the consumption of tile t,
+// so a single CTA barrier per tile covers both and no warp waits for a separate
+// production phase.  CTAs are
 // persistent and take work items (instance, id block, odd pattern, even chunk)
 // from a device counter, so boxes of different shapes share one launch.
 #include <cuda_runtime.h>
@@ -141,18 +144,17 @@ struct Cfg {
   static_assert(NW >= 4, "warp tables are written in groups of four");
 };
 
-// Stage tile t's records (bulk copy issued two tiles ahead) and turn them into
-// this CTA's coefficient records: one thread per conformation.  Ends with a
-// CTA barrier; returns false if a bounded wait gave up.
+// Turn tile t's staged records (bulk copy issued two tiles ahead) into this CTA's coefficient
+// records in buffer t & 1: one thread per conformation.  No barrier: the caller's next CTA barrier
+// publishes the records; a bounded wait that gives up raises *s_abort.
 template <class K>
-__device__ __forceinline__ bool produce_tile(const hp::PhenInst& in, unsigned* err, int t, uint32_t* rawbuf,
-                                             uint32_t* coefbuf, uint64_t* bars, unsigned (&issued)[2],
+__device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* err, int t, uint32_t* rawbuf,
+                                             uint32_t* coefbuf, uint64_t* bars,
                                              unsigned (&waited)[2], uint32_t o, uint32_t ehigh, int nroles,
                                              int* s_abort) {
   constexpr int R = K::R, T = K::T;
   const int tid = threadIdx.x;
   const int buf = t & 1;
-  const unsigned raw_bytes = (unsigned)(T * in.rec_words * 4);
   uint32_t* cbuf = coefbuf + buf * T * K::CSTRIDE;
   if (tid < T) {
     if (!mbar_wait(&bars[buf], waited[buf] & 1u)) {
@@ -208,12 +210,24 @@ __device__ __forceinline__ bool produce_tile(const hp::PhenInst& in, unsigned* e
     }
   }
   waited[buf]++;
+}
+
+// produce_work for tile t, then a CTA barrier and the bulk copy of tile t + 2 into the raw buffer
+// it has just freed; returns false if a bounded wait gave up.
+template <class K>
+__device__ __forceinline__ bool produce_tile(const hp::PhenInst& in, unsigned* err, int t, uint32_t* rawbuf,
+                                             uint32_t* coefbuf, uint64_t* bars, unsigned (&issued)[2],
+                                             unsigned (&waited)[2], uint32_t o, uint32_t ehigh, int nroles,
+                                             int* s_abort) {
+  constexpr int T = K::T;
+  produce_work<K>(in, err, t, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, s_abort);
   __syncthreads();
   if (*s_abort) return false;
-  // raw[buf] has been read by every producer: prefetch tile t + 2 into it
+  const int buf = t & 1;
   if (t + 2 < in.ntiles) {
-    if (tid == 0)
-      bulk_load(rawbuf + buf * T * in.rec_words, in.rec + (size_t)(t + 2) * T * in.rec_words, raw_bytes, &bars[buf]);
+    if (threadIdx.x == 0)
+      bulk_load(rawbuf + buf * T * in.rec_words, in.rec + (size_t)(t + 2) * T * in.rec_words,
+                (unsigned)(T * in.rec_words * 4), &bars[buf]);
     issued[buf]++;
   }
   return true;
@@ -290,33 +304,44 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
 #pragma unroll
     for (int v = 0; v < P; v++) tmax[v] = m1[v] = ts[v] = 0u;
     prefetch_first_tiles<T>(in, rawbuf, bars, issued);
-    for (int t = 0; t < in.ntiles; t++) {
-      if (!produce_tile<K>(in, p.ctrl, t, rawbuf, coefbuf, bars, issued, waited, o, ehigh, nroles, &s_abort)) break;
+    // coefficient records of tile t + 1 are produced halfway through the consumption of tile t
+    // (double buffered), so one barrier per tile covers both and no warp idles while others produce
+    produce_work<K>(in, p.ctrl, 0, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort);
+    __syncthreads();
+    if (!s_abort && in.ntiles > 2) {
+      if (tid == 0)
+        bulk_load(rawbuf, in.rec + (size_t)2 * T * in.rec_words, (unsigned)(T * in.rec_words * 4), &bars[0]);
+      issued[0]++;
+    }
+    for (int t = 0; t < in.ntiles && !s_abort; t++) {
       const uint32_t* cbuf = coefbuf + (t & 1) * T * CSTRIDE;
+      auto consume = [&](int s0, int s1) {
 #pragma unroll 2
-      for (int s = 0; s < T; s++) {
-        const uint32_t* cs = cbuf + s * CSTRIDE;
-        uint32_t tpv[K::TP_WORDS];
+        for (int s = s0; s < s1; s++) {
+          const uint32_t* cs = cbuf + s * CSTRIDE;
+          uint32_t tpv[K::TP_WORDS];
 #pragma unroll
-        for (int j = 0; j < K::TP_WORDS; j += 4) {
-          const uint4 q = *reinterpret_cast<const uint4*>(cs + K::TP_OFF + j);
-          tpv[j] = q.x; tpv[j + 1] = q.y; tpv[j + 2] = q.z; tpv[j + 3] = q.w;
-        }
-        // subset sums over the tree roles (IMAD: x * one + a keeps them on the FMA pipe); the
-        // leaves (top tree bit set) use the fused add + max
-        uint32_t x[P / 2];
-        x[0] = cs[lane] * p.one + cs[K::WT_OFF + warp];
+          for (int j = 0; j < K::TP_WORDS; j += 4) {
+            const uint4 q = *reinterpret_cast<const uint4*>(cs + K::TP_OFF + j);
+            tpv[j] = q.x; tpv[j + 1] = q.y; tpv[j + 2] = q.z; tpv[j + 3] = q.w;
+          }
+          uint32_t x[P / 2];
+          x[0] = cs[lane] * p.one + cs[K::WT_OFF + warp];
 #pragma unroll
-        for (int v = 1; v < P / 2; v++) {
-          const int hb = 31 - __clz(v);
-          x[v] = x[v ^ (1 << hb)] * p.one + tpv[hb];
-        }
+          for (int v = 1; v < P / 2; v++) {
+            const int hb = 31 - __clz(v);
+            x[v] = x[v ^ (1 << hb)] * p.one + tpv[hb];
+          }
 #pragma unroll
-        for (int v = 0; v < P / 2; v++) {
-          tmax[v] = vmax2(tmax[v], x[v]);
-          tmax[v + P / 2] = __viaddmax_u16x2(x[v], tpv[R - 2], tmax[v + P / 2]);
+          for (int v = 0; v < P / 2; v++) {
+            tmax[v] = vmax2(tmax[v], x[v]);
+            tmax[v + P / 2] = __viaddmax_u16x2(x[v], tpv[R - 2], tmax[v + P / 2]);
+          }
         }
-      }
+      };
+      consume(0, T / 2);
+      if (t + 1 < in.ntiles) produce_work<K>(in, p.ctrl, t + 1, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort);
+      consume(T / 2, T);
       // tile merge: best (doubled) with tie bit, and first tile reaching it
       const uint32_t tpk = (uint32_t)t * 0x10001u;
 #pragma unroll
@@ -327,6 +352,14 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         m1[v] = (gt & tmax[v]) | (~gt & (m1[v] | (eq & 0x00010001u)));
         ts[v] = (gt & tpk) | (~gt & ts[v]);
         tmax[v] = 0u;
+      }
+      __syncthreads();
+      // raw[(t + 1) & 1] has been read by the producers of tile t + 1: refill it with tile t + 3
+      if (!s_abort && t + 3 < in.ntiles) {
+        if (tid == 0)
+          bulk_load(rawbuf + ((t + 1) & 1) * T * in.rec_words, in.rec + (size_t)(t + 3) * T * in.rec_words,
+                    (unsigned)(T * in.rec_words * 4), &bars[(t + 1) & 1]);
+        issued[(t + 1) & 1]++;
       }
     }
     if (s_abort) break;
