@@ -371,6 +371,8 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (one JSON line)")
     ap.add_argument("--stream", default=None, metavar="BOX:BITS[:WINDOW[:DIR]]",
                     help="whole-space map of BOX in 2^BITS shards with exact designability and Eq. 2 statistics")
+    ap.add_argument("--train-case", action="store_true",
+                    help="time the proposal network's training step alone (batch 4096, 3x3x3 classes)")
     ap.add_argument("--proposal-case", action="store_true",
                     help="profiling case: top-4 proposals of an untrained 3x3x3 network for 65,536 ids, W + K times")
     ap.add_argument("--map-only", default=None, metavar="BOX:BITS",
@@ -400,6 +402,35 @@ def main():
     N, S, Sdir = s.N, s.S, s.S_dir
     if args.learned_only:
         print(json.dumps({"metric": METRIC, "learned": learned_leg(hp, s, torch)}))
+        return 0
+    if args.train_case:
+        from paper_2008_05612_gb300 import inputs
+
+        params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
+                  inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
+                  inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
+        batch = 4096
+        net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
+        ids_np = inputs.sample_ids(N, batch * 8, seed=321)
+        ids = torch.from_numpy(ids_np.view(np.int64)).cuda()
+        labels = torch.from_numpy((inputs.splitmix64(ids_np) % np.uint64(S)).astype(np.int32)).cuda()
+        chunks = [(ids[i * batch:(i + 1) * batch].contiguous(), labels[i * batch:(i + 1) * batch].contiguous())
+                  for i in range(8)]
+        for i in range(args.warmup):
+            net.train_step(*chunks[i % 8], 1e-3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.steps):
+            net.train_step(*chunks[i % 8], 1e-3)
+        e1.record()
+        torch.cuda.synchronize()
+        net.status()
+        ms = e0.elapsed_time(e1) / args.steps
+        # forward 2 B (N*512 + 512*512 + 512*S) + backward twice that, per id
+        flops = 6.0 * batch * (N * 512 + 512 * 512 + 512 * S)
+        print(json.dumps({"case": "training step, batch 4096, 3x3x3 classes", "ms_per_step": ms,
+                          "gemm_tflops_equiv": flops / (ms * 1e-3) / 1e12}))
         return 0
     if args.proposal_case:
         from paper_2008_05612_gb300 import inputs

@@ -238,19 +238,45 @@ __global__ void __launch_bounds__(256, 1) gemm_tn_big(const Gemm g) {
 
 // ------------------------------------------------------------------ small kernels
 
-// out[c, r] = in[r, c] for r < rows, c < cols; zero in [rows, out_cols) of each output row
+// out[c, r] = in[r, c] for r < rows, c < cols; zero in [rows, out_cols) of each output row.
+// 64 x 64 tiles; reads and writes move bf16 pairs (4 bytes), so a warp touches 128 contiguous
+// bytes of a row on both sides.
 __global__ void transpose_bf16(const bf16* __restrict__ in, int ldin, int rows, int cols, bf16* __restrict__ out,
                                int ldout, int out_cols) {
-  __shared__ bf16 tile[32][33];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int r = r0 + j, c = c0 + threadIdx.x;
-    tile[j][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ldin + c] : __float2bfloat16(0.f);
+  __shared__ bf16 tile[64][66];
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int j = ty; j < 64; j += 8) {
+    const int r = r0 + j, c = c0 + 2 * tx;
+    bf16 a = __float2bfloat16(0.f), b = a;
+    if (r < rows) {
+      if (c + 1 < cols && ((ldin | c) & 1) == 0) {
+        const __nv_bfloat162 q = *reinterpret_cast<const __nv_bfloat162*>(in + (size_t)r * ldin + c);
+        a = q.x;
+        b = q.y;
+      } else {
+        if (c < cols) a = in[(size_t)r * ldin + c];
+        if (c + 1 < cols) b = in[(size_t)r * ldin + c + 1];
+      }
+    }
+    tile[j][2 * tx] = a;
+    tile[j][2 * tx + 1] = b;
   }
   __syncthreads();
-  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-    const int c = c0 + j, r = r0 + threadIdx.x;
-    if (c < cols && r < out_cols) out[(size_t)c * ldout + r] = tile[threadIdx.x][j];
+  for (int j = ty; j < 64; j += 8) {
+    const int c = c0 + j, r = r0 + 2 * tx;
+    if (c >= cols) continue;
+    const bf16 a = tile[2 * tx][j], b = tile[2 * tx + 1][j];
+    bf16* o = out + (size_t)c * ldout + r;
+    if (r + 1 < out_cols && ((ldout | r) & 1) == 0) {
+      __nv_bfloat162 q;
+      q.x = a;
+      q.y = b;
+      *reinterpret_cast<__nv_bfloat162*>(o) = q;
+    } else {
+      if (r < out_cols) o[0] = a;
+      if (r + 1 < out_cols) o[1] = b;
+    }
   }
 }
 
@@ -270,54 +296,118 @@ __global__ void encode_bits(const unsigned long long* __restrict__ ids, int n, i
 
 // One block per row: loss += logsumexp(z) - z[label]; dz = (softmax(z) - onehot) * scale (bf16,
 // zero in padding columns); rows with label < 0 get dz = 0 and no loss.
+// Per labelled row: dZ = (softmax(z) - onehot(label)) * scale (bf16, zero past S and for
+// label -1) and the row's loss log(sum exp z) - z[label] added to *loss.  One block per row: an
+// online max / sum of exponentials over float4 loads, then one pass writing four bf16 at a time.
 __global__ void softmax_xent(const float* __restrict__ Z, int ldz, int S, const int32_t* __restrict__ labels,
                              bf16* __restrict__ dZ, int lddz, int Spad, float scale, float* __restrict__ loss) {
   const int row = blockIdx.x;
   const float* z = Z + (size_t)row * ldz;
   bf16* d = dZ + (size_t)row * lddz;
   const int lab = labels[row];
-  __shared__ float red[32];
-  float m = -INFINITY;
-  for (int c = threadIdx.x; c < S; c += blockDim.x) m = fmaxf(m, z[c]);
-  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : -INFINITY;
-    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-    if (threadIdx.x == 0) red[0] = v;
+  __shared__ float red_m[32], red_s[32];
+  float m = -INFINITY, sum = 0.f;
+  auto add = [&](float v) {  // online update of (max, sum of exp(. - max))
+    if (v > m) {
+      sum = sum * __expf(m - v) + 1.f;
+      m = v;
+    } else {
+      sum += __expf(v - m);
+    }
+  };
+  const int S4 = S & ~3;
+  for (int c = 4 * threadIdx.x; c < S4; c += 4 * blockDim.x) {
+    const float4 q = *reinterpret_cast<const float4*>(z + c);
+    add(q.x);
+    add(q.y);
+    add(q.z);
+    add(q.w);
+  }
+  for (int c = S4 + threadIdx.x; c < S; c += blockDim.x) add(z[c]);
+  // combine (m, sum) pairs: warp, then block
+  for (int o = 16; o; o >>= 1) {
+    const float om = __shfl_xor_sync(0xFFFFFFFFu, m, o), os = __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    const float nm = fmaxf(m, om);
+    sum = (m == -INFINITY ? 0.f : sum * __expf(m - nm)) + (om == -INFINITY ? 0.f : os * __expf(om - nm));
+    m = nm;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_m[threadIdx.x >> 5] = m;
+    red_s[threadIdx.x >> 5] = sum;
   }
   __syncthreads();
-  m = red[0];
-  __syncthreads();
-  float sum = 0.f;
-  for (int c = threadIdx.x; c < S; c += blockDim.x) sum += __expf(z[c] - m);
-  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
-  __syncthreads();
   if (threadIdx.x < 32) {
-    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    if (threadIdx.x == 0) red[0] = v;
+    const bool have = threadIdx.x < (blockDim.x >> 5);
+    m = have ? red_m[threadIdx.x] : -INFINITY;
+    sum = have ? red_s[threadIdx.x] : 0.f;
+    for (int o = 16; o; o >>= 1) {
+      const float om = __shfl_xor_sync(0xFFFFFFFFu, m, o), os = __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+      const float nm = fmaxf(m, om);
+      sum = (m == -INFINITY ? 0.f : sum * __expf(m - nm)) + (om == -INFINITY ? 0.f : os * __expf(om - nm));
+      m = nm;
+    }
+    if (threadIdx.x == 0) {
+      red_m[0] = m;
+      red_s[0] = sum;
+    }
   }
   __syncthreads();
-  sum = red[0];
+  m = red_m[0];
+  sum = red_s[0];
   const float inv = 1.f / sum;
-  for (int c = threadIdx.x; c < Spad; c += blockDim.x) {
-    float v = 0.f;
-    if (lab >= 0 && c < S) v = (__expf(z[c] - m) * inv - (c == lab ? 1.f : 0.f)) * scale;
-    d[c] = __float2bfloat16(v);
+  for (int c = 4 * threadIdx.x; c < Spad; c += 4 * blockDim.x) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (lab >= 0) {
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (c + j < S) v[j] = (__expf(z[c + j] - m) * inv - (c + j == lab ? 1.f : 0.f)) * scale;
+    }
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 w;
+    w.x = *reinterpret_cast<const uint32_t*>(&lo);
+    w.y = *reinterpret_cast<const uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(d + c) = w;
   }
   if (threadIdx.x == 0 && lab >= 0) atomicAdd(loss, logf(sum) + m - z[lab]);
 }
 
-// out[c] = sum over rows of in[r, c] (bf16 in, fp32 out)
-__global__ void colsum_bf16(const bf16* __restrict__ in, int ld, int rows, int cols, float* __restrict__ out) {
+// Column sums in two deterministic stages: part[chunk, c] = sum of the chunk's rows (256 rows per
+// chunk, two columns per thread from bf16 pairs), then out[c] = sum of part[., c] in chunk order.
+constexpr int kColChunk = 256;
+__global__ void colsum_partial(const bf16* __restrict__ in, int ld, int rows, int cols, float* __restrict__ part) {
+  const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (c >= cols) return;
+  const int r0 = blockIdx.y * kColChunk, r1 = min(rows, r0 + kColChunk);
+  float s0 = 0.f, s1 = 0.f;
+  if (c + 1 < cols) {
+    for (int r = r0; r < r1; r++) {
+      const __nv_bfloat162 q = *reinterpret_cast<const __nv_bfloat162*>(in + (size_t)r * ld + c);
+      s0 += __low2float(q);
+      s1 += __high2float(q);
+    }
+  } else {
+    for (int r = r0; r < r1; r++) s0 += __bfloat162float(in[(size_t)r * ld + c]);
+  }
+  part[(size_t)blockIdx.y * cols + c] = s0;
+  if (c + 1 < cols) part[(size_t)blockIdx.y * cols + c + 1] = s1;
+}
+
+__global__ void colsum_final(const float* __restrict__ part, int chunks, int cols, float* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= cols) return;
   float s = 0.f;
-  for (int r = 0; r < rows; r++) s += __bfloat162float(in[(size_t)r * ld + c]);
+  for (int k = 0; k < chunks; k++) s += part[(size_t)k * cols + c];
   out[c] = s;
+}
+
+// dA = (sum of the split-K partial products) * (H > 0), bf16 out
+__global__ void splitk_relu_backward(const float* __restrict__ part, int splits, size_t stride, const bf16* __restrict__ H,
+                                     bf16* __restrict__ dA, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int k = 0; k < splits; k++) v += part[k * stride + i];
+    dA[i] = __float2bfloat16(__bfloat162float(H[i]) > 0.f ? v : 0.f);
+  }
 }
 
 // dA = dH * (H > 0), fp32 in, bf16 out
@@ -444,6 +534,10 @@ struct hp_mlp {
   // fused top-k: per row up to 16 candidates of each of up to 2 lists per 256-class tile
   float* cand_v = nullptr;
   int32_t* cand_i = nullptr;
+  // column-sum partials (max_batch / 256 + 1 chunks x the widest layer) and split-K partial
+  // products of the output layer's input gradient (kSplitK x max_batch x H2)
+  float* colws = nullptr;
+  float* splitws = nullptr;
   int steps = 0;
 };
 
@@ -485,11 +579,19 @@ int gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, co
 }
 
 void transpose(const bf16* in, int ldin, int rows, int cols, bf16* out, int ldout, int out_cols, cudaStream_t st) {
-  dim3 grid((cols + 31) / 32, (std::max(rows, out_cols) + 31) / 32);
+  dim3 grid((cols + 63) / 64, (std::max(rows, out_cols) + 63) / 64);
   transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(in, ldin, rows, cols, out, ldout, out_cols);
 }
 
 int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
+
+constexpr int kSplitK = 8;
+
+void colsum(const bf16* in, int ld, int rows, int cols, float* out, float* ws, cudaStream_t st) {
+  const int chunks = (rows + kColChunk - 1) / kColChunk;
+  colsum_partial<<<dim3((cols + 255) / 256, chunks), 128, 0, st>>>(in, ld, rows, cols, ws);
+  colsum_final<<<(cols + 255) / 256, 256, 0, st>>>(ws, chunks, cols, out);
+}
 
 // Hidden layers for rows [0, rows) whose ids are in `ids` (n valid) -> m->Hb2
 int forward_hidden(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
@@ -515,21 +617,33 @@ int backward(hp_mlp* m, int n, int rows, cudaStream_t st) {
   cudaMemsetAsync(m->loss, 0, sizeof(float), st);
   softmax_xent<<<rows, 256, 0, st>>>(m->Z, Spad, S, m->labels, m->dZ, Spad, Spad, 1.f / (float)std::max(n, 1), m->loss);
   // layer 3
-  colsum_bf16<<<(S + 255) / 256, 256, 0, st>>>(m->dZ, Spad, rows, S, m->g[5]);
+  colsum(m->dZ, Spad, rows, S, m->g[5], m->colws, st);
   transpose(m->dZ, Spad, rows, Spad, m->dZT, rows, rows, st);
   transpose(m->Hb2, H2, rows, H2, m->H2T, rows, rows, st);
   if (rc == HP_OK) rc = gemm(m->dZT, rows, m->H2T, rows, S, H2, rows, nullptr, 0, m->g[4], H2, nullptr, 0, st, m->tc_err);
-  if (rc == HP_OK) rc = gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, nullptr, 0, m->dHf, H2, nullptr, 0, st, m->tc_err);
-  relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->dHf, m->Hb2, m->dA2, (size_t)rows * H2);
+  if (tc_enabled()) {
+    // rows x H2 output with a Spad-long contraction: too few tiles for the GPU, so split K
+    hp::TcEpilogue ep;
+    ep.Cf = m->splitws;
+    ep.ldcf = H2;
+    ep.ksplit = std::min(kSplitK, (Spad + 63) / 64);
+    ep.split_stride = (size_t)rows * H2;
+    if (rc == HP_OK) rc = hp::tc_gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, ep, m->tc_err, st);
+    splitk_relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->splitws, ep.ksplit, ep.split_stride, m->Hb2,
+                                                                      m->dA2, (size_t)rows * H2);
+  } else {
+    if (rc == HP_OK) rc = gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, nullptr, 0, m->dHf, H2, nullptr, 0, st, m->tc_err);
+    relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->dHf, m->Hb2, m->dA2, (size_t)rows * H2);
+  }
   // layer 2
-  colsum_bf16<<<(H2 + 255) / 256, 256, 0, st>>>(m->dA2, H2, rows, H2, m->g[3]);
+  colsum(m->dA2, H2, rows, H2, m->g[3], m->colws, st);
   transpose(m->dA2, H2, rows, H2, m->dA2T, rows, rows, st);
   transpose(m->Hb1, H1, rows, H1, m->H1T, rows, rows, st);
   if (rc == HP_OK) rc = gemm(m->dA2T, rows, m->H1T, rows, H2, H1, rows, nullptr, 0, m->g[2], H1, nullptr, 0, st, m->tc_err);
   if (rc == HP_OK) rc = gemm(m->dA2, H2, m->w2t, H2, rows, H1, H2, nullptr, 0, m->dHf, H1, nullptr, 0, st, m->tc_err);
   relu_backward<<<grid_for((size_t)rows * H1), 256, 0, st>>>(m->dHf, m->Hb1, m->dA1, (size_t)rows * H1);
   // layer 1
-  colsum_bf16<<<(H1 + 255) / 256, 256, 0, st>>>(m->dA1, H1, rows, H1, m->g[1]);
+  colsum(m->dA1, H1, rows, H1, m->g[1], m->colws, st);
   transpose(m->dA1, H1, rows, H1, m->dA1T, rows, rows, st);
   transpose(m->X, Kin, rows, Kin, m->XT, rows, rows, st);
   if (rc == HP_OK) rc = gemm(m->dA1T, rows, m->XT, rows, H1, Kin, rows, nullptr, 0, m->g[0], Kin, nullptr, 0, st, m->tc_err);
@@ -554,7 +668,8 @@ void free_model(hp_mlp* m) {
     cudaFree(m->v[i]);
   }
   void* ptrs[] = {m->w1b, m->w2b, m->w3b, m->w2t, m->w3t, m->X,  m->XT,  m->Hb1, m->Hb2,  m->H1T,  m->H2T,
-                  m->Z,   m->dHf, m->loss, m->dZ,  m->dZT, m->dA2, m->dA2T, m->dA1, m->dA1T, m->labels, m->tc_err, m->cand_v, m->cand_i};
+                  m->Z,   m->dHf, m->loss, m->dZ,  m->dZT, m->dA2, m->dA2T, m->dA1, m->dA1T, m->labels, m->tc_err, m->cand_v, m->cand_i,
+                  m->colws, m->splitws};
   for (void* p : ptrs) cudaFree(p);
   delete m;
 }
@@ -623,6 +738,8 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
   const size_t ncand = (size_t)max_batch * ((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcListsPerTile * 16;
   al(&m->cand_v, ncand * 4);
   al(&m->cand_i, ncand * 4);
+  al(&m->colws, (size_t)(B / kColChunk + 1) * std::max(m->Spad, std::max(H1, H2)) * 4);
+  al(&m->splitws, (size_t)kSplitK * B * H2 * 4);
   if (e != cudaSuccess) {
     free_model(m);
     return hp::cuda_fail(e, "hp_mlp_create: device allocation");

@@ -3,13 +3,14 @@
 // One persistent CTA per SM walks the 128 x 256 output tiles (m fastest, so the CTAs running at
 // the same time share B tiles in L2).  Warp roles:
 //   warp 0, one lane  TMA producer: 64-wide K chunks of A (128 x 64) and B (256 x 64) into a
-//                     4-stage ring, 128-byte swizzled, completion counted on full[s];
+//                     3-stage ring, 128-byte swizzled, completion counted on full[s];
 //   warp 1, one lane  MMA issuer: four tcgen05.mma (M 128, N 256, K 16) per chunk into one of two
 //                     tensor-memory accumulators (2 x 256 columns), commit -> empty[s] frees the
 //                     stage, commit -> tmem_full[a] hands the finished accumulator over;
-//   warps 2..5        epilogue: tcgen05.ld (warp w reads lanes 32 (w % 4) .. +31 = tile rows),
-//                     bias, ReLU, stores through a padded shared-memory square (coalesced rows),
-//                     or a per-row running top-k; then arrive on tmem_empty[a].
+//   warps 2..9        epilogue, two warps per lane quarter and 128 columns each: tcgen05.ld
+//                     (warp w reads lanes 32 (w % 4) .. +31 = tile rows), bias, ReLU, stores
+//                     through a padded shared-memory square (coalesced rows), or a per-row
+//                     running top-k; then arrive on tmem_empty[a].
 // With two accumulators the epilogue of tile i overlaps the MMAs of tile i + 1.  Every mbarrier
 // wait is bounded; one that gives up raises a shared abort flag (the other roles stop at their
 // next wait) and the device error word, and each role drains what it has in flight before the
@@ -34,16 +35,15 @@ constexpr int TM = kTcTileM, TN = kTcTileN, TK = 64;
 constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SQ_FLOATS = 32 * 33;  // store mode: one epilogue warp's padded 32 x 32 square
 constexpr int SX_FLOATS = 32 * 32;  // top-k mode: one epilogue warp's staged logits (XOR-swizzled rows)
-// store mode: 4 epilogue warps (one per tensor-memory lane quarter, all 256 columns of a tile);
-// top-k mode: 8 (two per quarter, 128 columns each), for twice the latency hiding
-// (top-k mode also keeps its warp's 128 biases of the current tile in shared memory, and runs a
-// 3-stage ring to make room)
+// 8 epilogue warps in both modes: two per tensor-memory lane quarter, 128 columns each (top-k
+// mode also keeps its warp's 128 biases of the current tile in shared memory); a 3-stage ring
+// leaves room for their shared-memory areas
 template <int KT>
 struct Shape {
-  static constexpr int kEpiWarps = KT > 0 ? 4 * kTcListsPerTile : 4;
+  static constexpr int kEpiWarps = 4 * kTcListsPerTile;
   static constexpr int kThreads = 64 + 32 * kEpiWarps;
   static constexpr int kColsPerWarp = TN / (kEpiWarps / 4);
-  static constexpr int kStages = KT > 0 ? 3 : 4;
+  static constexpr int kStages = 3;
   static constexpr int kAreaFloats = KT > 0 ? SX_FLOATS + kColsPerWarp : SQ_FLOATS;
   static constexpr int kSmem = kStages * STAGE_BYTES + kEpiWarps * kAreaFloats * 4 + 1024;
 };
@@ -52,19 +52,28 @@ constexpr uint32_t SPIN_LIMIT = 1u << 24;
 // Work unit u: m tile u % mt and the column tiles [r nt / nr, (r + 1) nt / nr) of r = u / mt.
 // Store mode uses one column tile per unit (nr = nt); top-k mode carries each row's list across
 // the tiles of a unit, so its threshold rises early and few columns need an insertion.
+// With split-K (store mode only) a unit is also one of ksplit slices of the K chunks.
 struct Params {
-  int M, N, K, mt, nt, nr, units;
+  int M, N, K, mt, nt, nr, units, ksplit;
   TcEpilogue ep;
   unsigned* err;
 };
 
 struct Unit {
-  int m0, nb, ne, r;
+  int m0, nb, ne, r, ks, kb, ke;  // ks: K slice; [kb, ke): its K chunks
 };
 
 __device__ __forceinline__ Unit unit_of(const Params& p, int u) {
-  const int r = u / p.mt;
-  return {(u % p.mt) * TM, (int)((long long)r * p.nt / p.nr), (int)((long long)(r + 1) * p.nt / p.nr), r};
+  const int nk = (p.K + TK - 1) / TK;
+  const int ks = u % p.ksplit, rest = u / p.ksplit;
+  const int r = rest / p.mt;
+  return {(rest % p.mt) * TM,
+          (int)((long long)r * p.nt / p.nr),
+          (int)((long long)(r + 1) * p.nt / p.nr),
+          r,
+          ks,
+          (int)((long long)ks * nk / p.ksplit),
+          (int)((long long)(ks + 1) * nk / p.ksplit)};
 }
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -166,7 +175,6 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const int nk = (p.K + TK - 1) / TK;
   unsigned* err = p.err;
 
   if (warp == 0 && lane == 0) {
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
     for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
       const Unit w = unit_of(p, u);
       for (int tn = w.nb; tn < w.ne && ok; tn++) {
-        for (int kc = 0; kc < nk; kc++, it++) {
+        for (int kc = w.kb; kc < w.ke; kc++, it++) {
           const uint32_t s = it % STAGES, r = it / STAGES;
           // round r reuses the stage after the MMAs of round r - 1 committed (round 0: fresh barrier)
           if (!wait_or_abort(&empty[s], (r & 1) ^ 1, abort_flag, err)) {
@@ -210,7 +218,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc_addr = tmem + a * TN;
-        for (int kc = 0; kc < nk; kc++, it++) {
+        for (int kc = w.kb; kc < w.ke; kc++, it++) {
           const uint32_t s = it % STAGES, r = it / STAGES;
           if (!wait_or_abort(&full[s], r & 1, abort_flag, err)) {
             ok = false;
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
           const uint32_t a_addr = sa(smem + s * STAGE_BYTES), b_addr = a_addr + A_BYTES;
 #pragma unroll
           for (int ks = 0; ks < TK / 16; ks++) {
-            const uint32_t accumulate = (kc | ks) ? 1u : 0u;
+            const uint32_t accumulate = (kc != w.kb || ks != 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                     acc_addr),
@@ -313,7 +321,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
                 const size_t row = (size_t)(rbase + r);
                 float x = area[r * 33 + lane] + bl;
                 if (ep.relu) x = fmaxf(x, 0.f);
-                if (ep.Cf) ep.Cf[row * ep.ldcf + cl] = x;
+                if (ep.Cf) ep.Cf[(size_t)w.ks * ep.split_stride + row * ep.ldcf + cl] = x;
                 if (ep.Cb) ep.Cb[row * ep.ldcb + cl] = __float2bfloat16(x);
               }
             }
@@ -545,9 +553,12 @@ int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
   int rc = make_map(&ma, A, M, K, lda, TM);
   if (rc == HP_OK) rc = make_map(&mb, B, N, K, ldb, TN);
   if (rc != HP_OK) return rc;
-  Params p{M, N, K, (M + TM - 1) / TM, (N + TN - 1) / TN, 0, 0, ep, err};
+  const int nk = (K + TK - 1) / TK;
+  if (ep.ksplit < 1 || ep.ksplit > nk || (ep.ksplit > 1 && (ep.kt || ep.Cb || ep.bias || ep.relu || !ep.Cf)))
+    return fail(HP_EINVAL, "tc_gemm: split-K needs store mode with an fp32 output only and at most one slice per K chunk");
+  Params p{M, N, K, (M + TM - 1) / TM, (N + TN - 1) / TN, 0, 0, ep.ksplit, ep, err};
   p.nr = ep.kt ? tc_topk_lists(M, N) / kTcListsPerTile : p.nt;
-  p.units = p.mt * p.nr;
+  p.units = p.mt * p.nr * p.ksplit;
   switch (ep.kt) {
     case 0: launch<0>(ma, mb, p, st); break;
     case 4: launch<4>(ma, mb, p, st); break;

@@ -29,6 +29,11 @@ struct TcEpilogue {
   int kt = 0;
   float* cand_v = nullptr;
   int32_t* cand_i = nullptr;
+  // split-K (store mode, fp32 output only, no bias / ReLU): the K chunks are cut into ksplit
+  // contiguous slices computed by different CTAs; slice j's partial product goes to
+  // Cf + j * split_stride, and the caller sums the slices
+  int ksplit = 1;
+  size_t split_stride = 0;
 };
 
 // Launch on `st`.  A bounded wait that gives up sets *err (device word, may be null) to nonzero
