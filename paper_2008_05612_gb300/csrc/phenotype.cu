@@ -27,7 +27,8 @@
 // A sequence whose best is reached in two tiles is not unique.  Pass 2 stages
 // the tiles again and resolves every other sequence exactly inside its one tile
 // (warp-cooperative count and first index with ballots), which also yields the
-// lowest-index conformation at the minimum.
+// lowest-index conformation at the minimum; each thread keeps a bit mask of its
+// unresolved candidates, so it only reads those fields.
 //
 // Data movement.  Conformation records (contact masks, see hp_internal.h) are
 // staged tile by tile into shared memory with the bulk-copy engine
@@ -366,7 +367,9 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
 
     // ================= classify: a field stays a candidate (best >= 2) only if its
     // minimum was reached in a single tile (or labels are wanted); others resolve to -1
+    // (cmask: bit 2v + h marks an unresolved candidate, so pass 2 visits only those fields)
     int next_tile = 0x7FFFFFFF;
+    unsigned long long cmask = 0;  // 2P <= 64 fields
 #pragma unroll
     for (int v = 0; v < P; v++) {
       uint32_t mv = m1[v], tv = ts[v];
@@ -381,6 +384,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
           tv |= 0xFFFFu << (16 * h);
         } else {
           next_tile = min(next_tile, (int)((tv >> (16 * h)) & 0xFFFFu));
+          cmask |= 1ull << (2 * v + h);
         }
       }
       st_best[v * kThreads + tid] = mv;
@@ -398,14 +402,11 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         int f = -1;
         uint32_t fld = 0;
         if (need) {
-          for (int v = 0; v < P && f < 0; v++) {
-            const uint32_t mv = st_best[v * kThreads + tid], tv = st_tile[v * kThreads + tid];
-            for (int h = 0; h < 2; h++) {
-              const uint32_t fb = (mv >> (16 * h)) & 0xFFFFu;
-              if (f < 0 && fb >= 2u && ((tv >> (16 * h)) & 0xFFFFu) == (uint32_t)t) {
-                f = 2 * v + h;
-                fld = fb;
-              }
+          for (unsigned long long m = cmask; m && f < 0; m &= m - 1) {
+            const int c = __ffsll((long long)m) - 1, v = c >> 1, h = c & 1;
+            if (((st_tile[v * kThreads + tid] >> (16 * h)) & 0xFFFFu) == (uint32_t)t) {
+              f = c;
+              fld = (st_best[v * kThreads + tid] >> (16 * h)) & 0xFFFFu;
             }
           }
           if (f < 0) need = false;
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
             count += __popc(bal);
           }
           if (lane == src) {
+            cmask &= ~(1ull << sf);
             const int cls = first >= 0 ? in.conf_class[first] : -1;
             const bool unique = !(sfld & 1u) && count == 1;
             const uint32_t sh = 16 * h;
@@ -443,10 +445,9 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       }
       if (next_tile == t) {
         next_tile = 0x7FFFFFFF;
-        for (int v = 0; v < P; v++) {
-          const uint32_t mv = st_best[v * kThreads + tid], tv = st_tile[v * kThreads + tid];
-          for (int h = 0; h < 2; h++)
-            if (((mv >> (16 * h)) & 0xFFFFu) >= 2u) next_tile = min(next_tile, (int)((tv >> (16 * h)) & 0xFFFFu));
+        for (unsigned long long m = cmask; m; m &= m - 1) {
+          const int c = __ffsll((long long)m) - 1;
+          next_tile = min(next_tile, (int)((st_tile[(c >> 1) * kThreads + tid] >> (16 * (c & 1))) & 0xFFFFu));
         }
       }
     }
