@@ -170,35 +170,41 @@ __device__ __forceinline__ int32_t cc_find(const int32_t* label, int32_t x) {
   return x;
 }
 
-// Lock-free union: hook the larger root under the smaller one with a CAS and
-// retry from the value the CAS saw.  Every failed CAS means another thread
-// linked that root, so the loop makes progress; it is bounded all the same.
+// Lock-free union of the components of a and b: hook the larger root under the smaller one with
+// a CAS and retry from the value the CAS saw.  Every failed CAS means another thread linked that
+// root, so the loop makes progress; it is bounded all the same (false if it gives up).
+__device__ __forceinline__ bool cc_union(int32_t* label, int32_t a, int32_t b) {
+  for (int tries = 0; tries < (1 << 24); tries++) {
+    const int32_t ra = cc_find(label, a), rb = cc_find(label, b);
+    if (ra == rb) return true;
+    const int32_t lo = min(ra, rb), hi = max(ra, rb);
+    const int32_t seen = atomicCAS(label + hi, hi, lo);
+    if (seen == hi) return true;
+    a = lo;
+    b = seen;
+  }
+  return false;
+}
+
+// One warp per 32 consecutive ids: the (id, flipped bit) pairs of its non-deleterious ids are
+// spread over the lanes (about 1.5 such ids per 32 in 3x3x3), so the partner reads and unions of
+// different pairs are in flight together instead of one lane walking all N bits.
 __global__ void cc_hook(const int32_t* __restrict__ phen, int N, int32_t* label, unsigned* __restrict__ err) {
   const unsigned long long total = 1ull << N;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-    if (__ldcg(label + g) < 0) continue;  // deleterious or out of range
-    const int32_t p = __ldg(phen + g);
-    for (int i = 0; i < N; i++) {
-      const unsigned long long h = g ^ (1ull << i);
-      if (h < g || __ldg(phen + h) != p) continue;
-      int32_t a = (int32_t)g, b = (int32_t)h;
-      bool done = false;
-      for (int tries = 0; tries < (1 << 24) && !done; tries++) {
-        const int32_t ra = cc_find(label, a), rb = cc_find(label, b);
-        if (ra == rb) {
-          done = true;
-          break;
-        }
-        const int32_t lo = min(ra, rb), hi = max(ra, rb);
-        const int32_t seen = atomicCAS(label + hi, hi, lo);
-        if (seen == hi) done = true;
-        else {
-          a = lo;
-          b = seen;
-        }
-      }
-      if (!done) atomicOr(err, kErrUnion);
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  for (unsigned long long base = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+       base < total; base += warps * 32) {
+    const unsigned long long g = base + lane;
+    const bool fold = g < total && __ldcg(label + g) >= 0;  // deleterious ids carry label -1
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fold);
+    const int npairs = __popc(bal) * N;
+    for (int k = lane; k < npairs; k += 32) {
+      const int src = __fns(bal, 0, k / N + 1), i = k % N;
+      const unsigned long long gs = base + src, h = gs ^ (1ull << i);
+      if (h < gs) continue;  // each pair once, from its smaller id
+      if (__ldg(phen + h) != __ldg(phen + gs)) continue;
+      if (!cc_union(label, (int32_t)gs, (int32_t)h)) atomicOr(err, kErrUnion);
     }
   }
 }
