@@ -30,7 +30,7 @@ DIMS = (3, 3, 3)
 WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformations (51,704 classes)"
 # DRAM bytes (read + write) of one full 3x3x3 phenotype-kernel launch, from the ncu capture summarised in
 # profiles/phenotype_kernel_3x3x3.md; None whenever the kernel has changed since the last capture.
-TRAFFIC_PER_LAUNCH = 1_769_066_752
+TRAFFIC_PER_LAUNCH = 1_770_234_368
 
 
 def dist_env():
