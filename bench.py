@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 METRIC = "HP seq×struct evals/s & sequences/s (3x3x3, 6x6); learned-pruned vs plain"
 DIMS = (3, 3, 3)
 WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformations (51,704 classes)"
-# DRAM bytes (read + write) of one full 3x3x3 phenotype-kernel launch, from the ncu capture summarised in
-# profiles/phenotype_kernel_3x3x3.md; None whenever the kernel has changed since the last capture.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full 3x3x3 phenotype-kernel launch, from
+# an ncu capture of the current kernel; None whenever the kernel has changed since the last capture.
 TRAFFIC_PER_LAUNCH = 1_770_234_368
 
 
