@@ -36,8 +36,9 @@
 // conformation turns a record into the CTA's coefficient record (lane table,
 // warp table, packed tree coefficients) in a second double buffer; in pass 1 the
 // records of tile t + 1 are produced halfway through the consumption of tile t,
-// so a single CTA barrier per tile covers both and no warp waits for a separate
-// production phase.  CTAs are
+// and instead of a CTA barrier per tile the producer warps arrive on a "produced"
+// mbarrier per buffer and every warp on a "consumed" one, so each warp waits only
+// for the buffer it needs next (bounded waits).  CTAs are
 // persistent and take work items (instance, id block, odd pattern, even chunk)
 // from a device counter, so boxes of different shapes share one launch.
 #include <cuda_runtime.h>
@@ -81,9 +82,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                : "memory");
 }
 
-// Wait for phase `parity` of the barrier; false after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (long long i = 0; i < kSpinLimit; i++) {
+// Wait for phase `parity` of the barrier; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = kSpinLimit) {
+  for (long long i = 0; i < limit; i++) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -250,7 +251,8 @@ template <class K>
 __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_constant__ hp::PhenParams p) {
   constexpr int R = K::R, T = K::T, P = K::P, kThreads = K::THREADS, CSTRIDE = K::CSTRIDE;
   extern __shared__ __align__(128) uint32_t smem[];
-  // layout: [coef 2 x T x CSTRIDE][raw 2 x T x max_rec_words][state 2 x P x THREADS][2 mbarriers]
+  // layout: [coef 2 x T x CSTRIDE][raw 2 x T x max_rec_words][state 2 x P x THREADS][6 mbarriers:
+  // raw copies (2), coefficient buffer produced (2), coefficient buffer consumed (2)]
   uint32_t* coefbuf = smem;
   uint32_t* rawbuf = smem + K::kCoefWords;
   uint32_t* st_best = rawbuf + 2 * T * p.max_rec_words;  // [P][THREADS] packed best (doubled score | tie)
@@ -263,12 +265,18 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], T / 32);      // one arrival per producer warp
+    mbar_init(&bars[3], T / 32);
+    mbar_init(&bars[4], kThreads / 32);  // one arrival per warp
+    mbar_init(&bars[5], kThreads / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
   __syncthreads();
   // per raw buffer: bulk copies issued and waited for (identical in every thread)
   unsigned issued[2] = {0u, 0u}, waited[2] = {0u, 0u};
+  // per coefficient buffer: productions waited for, and consumptions arrived (identical in every thread)
+  unsigned fcnt0 = 0u, fcnt1 = 0u, ccnt0 = 0u, ccnt1 = 0u;
   const uint32_t role_hi = ((uint32_t)lane << R) | ((uint32_t)warp << (R + kLaneRoles));
 
   for (;;) {
@@ -306,16 +314,43 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     for (int v = 0; v < P; v++) tmax[v] = m1[v] = ts[v] = 0u;
     prefetch_first_tiles<T>(in, rawbuf, bars, issued);
     // coefficient records of tile t + 1 are produced halfway through the consumption of tile t
-    // (double buffered), so one barrier per tile covers both and no warp idles while others produce
-    produce_work<K>(in, p.ctrl, 0, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort);
-    __syncthreads();
-    if (!s_abort && in.ntiles > 2) {
-      if (tid == 0)
-        bulk_load(rawbuf, in.rec + (size_t)2 * T * in.rec_words, (unsigned)(T * in.rec_words * 4), &bars[0]);
-      issued[0]++;
-    }
-    for (int t = 0; t < in.ntiles && !s_abort; t++) {
-      const uint32_t* cbuf = coefbuf + (t & 1) * T * CSTRIDE;
+    // (double buffered).  No CTA barrier: the producer warps arrive on full[b] when a buffer is
+    // written, every warp arrives on empty[b] when it has consumed it, and a warp waits only for
+    // the buffer it needs next, so fast warps run ahead instead of idling at a barrier.
+    const bool producer = tid < T;
+    auto produce_and_publish = [&](int tp) {
+      const int b = tp & 1;
+      if (producer) {
+        // the previous contents of buffer b (tile tp - 2) must have been consumed by every warp
+        if (tp >= 2 && !mbar_wait(&bars[4 + b], ((b ? ccnt1 : ccnt0) - 1u) & 1u, 1ll << 22)) {
+          atomicOr(p.ctrl, kErrTimeout);
+          s_abort = 1;
+        }
+      }
+      produce_work<K>(in, p.ctrl, tp, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort);
+      if (producer) {
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bars[2 + b])) : "memory");
+      }
+    };
+    produce_and_publish(0);
+    for (int t = 0; t < in.ntiles; t++) {
+      const int b = t & 1;
+      if (!mbar_wait(&bars[2 + b], (b ? fcnt1 : fcnt0) & 1u, 1ll << 22)) {
+        atomicOr(p.ctrl, kErrTimeout);
+        s_abort = 1;
+      }
+      if (b) fcnt1++;
+      else fcnt0++;
+      if (s_abort) break;
+      // every producer has read raw[b] (tile t): refill it with tile t + 2
+      if (t + 2 < in.ntiles) {
+        if (tid == 0)
+          bulk_load(rawbuf + b * T * in.rec_words, in.rec + (size_t)(t + 2) * T * in.rec_words,
+                    (unsigned)(T * in.rec_words * 4), &bars[b]);
+        issued[b]++;
+      }
+      const uint32_t* cbuf = coefbuf + b * T * CSTRIDE;
       auto consume = [&](int s0, int s1) {
 #pragma unroll 2
         for (int s = s0; s < s1; s++) {
@@ -326,6 +361,8 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
             const uint4 q = *reinterpret_cast<const uint4*>(cs + K::TP_OFF + j);
             tpv[j] = q.x; tpv[j + 1] = q.y; tpv[j + 2] = q.z; tpv[j + 3] = q.w;
           }
+          // subset sums over the tree roles (IMAD: x * one + a keeps them on the FMA pipe); the
+          // leaves (top tree bit set) use the fused add + max
           uint32_t x[P / 2];
           x[0] = cs[lane] * p.one + cs[K::WT_OFF + warp];
 #pragma unroll
@@ -341,8 +378,13 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         }
       };
       consume(0, T / 2);
-      if (t + 1 < in.ntiles) produce_work<K>(in, p.ctrl, t + 1, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort);
+      if (t + 1 < in.ntiles) produce_and_publish(t + 1);
       consume(T / 2, T);
+      // this warp is done with buffer b
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bars[4 + b])) : "memory");
+      if (b) ccnt1++;
+      else ccnt0++;
       // tile merge: best (doubled) with tie bit, and first tile reaching it
       const uint32_t tpk = (uint32_t)t * 0x10001u;
 #pragma unroll
@@ -354,15 +396,8 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         ts[v] = (gt & tpk) | (~gt & ts[v]);
         tmax[v] = 0u;
       }
-      __syncthreads();
-      // raw[(t + 1) & 1] has been read by the producers of tile t + 1: refill it with tile t + 3
-      if (!s_abort && t + 3 < in.ntiles) {
-        if (tid == 0)
-          bulk_load(rawbuf + ((t + 1) & 1) * T * in.rec_words, in.rec + (size_t)(t + 3) * T * in.rec_words,
-                    (unsigned)(T * in.rec_words * 4), &bars[(t + 1) & 1]);
-        issued[(t + 1) & 1]++;
-      }
     }
+    __syncthreads();  // pass 2 re-stages the buffers: every warp is done with them
     if (s_abort) break;
 
     // ================= classify: a field stays a candidate (best >= 2) only if its
@@ -553,7 +588,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
 template <class K>
 size_t smem_bytes(int max_rec_words) {
   const size_t words = (size_t)K::kCoefWords + 2ull * K::T * max_rec_words + (size_t)K::kStateWords;
-  return words * 4 + 2 * sizeof(uint64_t);
+  return words * 4 + 6 * sizeof(uint64_t);
 }
 
 template <class K>
