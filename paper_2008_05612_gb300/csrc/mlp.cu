@@ -538,6 +538,9 @@ struct hp_mlp {
   // products of the output layer's input gradient (kSplitK x max_batch x H2)
   float* colws = nullptr;
   float* splitws = nullptr;
+  // training with the softmax in the output layer's epilogue: per-list row statistics, the
+  // label logit, and each row's max and 1 / sum
+  float *stats = nullptr, *zlab = nullptr, *row_m = nullptr, *row_inv = nullptr;
   int steps = 0;
 };
 
@@ -611,14 +614,17 @@ int forward(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStrea
 }
 
 // Gradients of the mean cross-entropy over the n valid rows into m->g[*]; loss sum into m->loss
-int backward(hp_mlp* m, int n, int rows, cudaStream_t st) {
+// (with have_dz, the logits' gradient dZ, its transpose dZT and the loss are already there)
+int backward(hp_mlp* m, int n, int rows, cudaStream_t st, bool have_dz = false) {
   int rc = HP_OK;
   const int S = m->S, H1 = m->H1, H2 = m->H2, Kin = m->Kin, Spad = m->Spad;
-  cudaMemsetAsync(m->loss, 0, sizeof(float), st);
-  softmax_xent<<<rows, 256, 0, st>>>(m->Z, Spad, S, m->labels, m->dZ, Spad, Spad, 1.f / (float)std::max(n, 1), m->loss);
+  if (!have_dz) {
+    cudaMemsetAsync(m->loss, 0, sizeof(float), st);
+    softmax_xent<<<rows, 256, 0, st>>>(m->Z, Spad, S, m->labels, m->dZ, Spad, Spad, 1.f / (float)std::max(n, 1), m->loss);
+  }
   // layer 3
   colsum(m->dZ, Spad, rows, S, m->g[5], m->colws, st);
-  transpose(m->dZ, Spad, rows, Spad, m->dZT, rows, rows, st);
+  if (!have_dz) transpose(m->dZ, Spad, rows, Spad, m->dZT, rows, rows, st);
   transpose(m->Hb2, H2, rows, H2, m->H2T, rows, rows, st);
   if (rc == HP_OK) rc = gemm(m->dZT, rows, m->H2T, rows, S, H2, rows, nullptr, 0, m->g[4], H2, nullptr, 0, st, m->tc_err);
   if (tc_enabled()) {
@@ -650,6 +656,44 @@ int backward(hp_mlp* m, int n, int rows, cudaStream_t st) {
   return rc;
 }
 
+// Loss and gradients of one batch.  On the tcgen05 path the softmax runs in the output layer's
+// epilogue: a first pass of the layer's GEMM keeps per-row maxima and sums of exponentials, a
+// second pass recomputes the logits and writes their gradient in both layouts, so the fp32 logits
+// never reach memory and no transpose of the gradient is needed.
+int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
+  if (!tc_enabled()) {
+    int rc = forward(m, ids, n, rows, st);
+    if (rc == HP_OK) rc = backward(m, n, rows, st);
+    return rc;
+  }
+  int rc = forward_hidden(m, ids, n, rows, st);
+  hp::TcEpilogue ea;
+  ea.kt = -1;
+  ea.bias = m->w[5];
+  ea.labels = m->labels;
+  ea.stats = m->stats;
+  ea.zlab = m->zlab;
+  if (rc == HP_OK) rc = hp::tc_gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, ea, m->tc_err, st);
+  if (rc != HP_OK) return rc;
+  cudaMemsetAsync(m->loss, 0, sizeof(float), st);
+  hp::tc_softmax_finish(m->stats, hp::tc_topk_lists(rows, m->S), rows, m->labels, m->zlab, m->row_m, m->row_inv, m->loss,
+                        st);
+  hp::TcEpilogue eb;
+  eb.kt = -2;
+  eb.bias = m->w[5];
+  eb.labels = m->labels;
+  eb.row_m = m->row_m;
+  eb.row_inv = m->row_inv;
+  eb.scale = 1.f / (float)std::max(n, 1);
+  eb.dz = m->dZ;
+  eb.ldz = m->Spad;
+  eb.dzt = m->dZT;
+  eb.ldzt = rows;
+  rc = hp::tc_gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, eb, m->tc_err, st);
+  if (rc == HP_OK) rc = backward(m, n, rows, st, true);
+  return rc;
+}
+
 // refresh the bf16 copies and transposes used by the forward and backward GEMMs
 void refresh_copies(hp_mlp* m, cudaStream_t st) {
   cast_bf16<<<grid_for(m->n[0]), 256, 0, st>>>(m->w[0], m->w1b, m->n[0]);
@@ -669,7 +713,7 @@ void free_model(hp_mlp* m) {
   }
   void* ptrs[] = {m->w1b, m->w2b, m->w3b, m->w2t, m->w3t, m->X,  m->XT,  m->Hb1, m->Hb2,  m->H1T,  m->H2T,
                   m->Z,   m->dHf, m->loss, m->dZ,  m->dZT, m->dA2, m->dA2T, m->dA1, m->dA1T, m->labels, m->tc_err, m->cand_v, m->cand_i,
-                  m->colws, m->splitws};
+                  m->colws, m->splitws, m->stats, m->zlab, m->row_m, m->row_inv};
   for (void* p : ptrs) cudaFree(p);
   delete m;
 }
@@ -740,6 +784,10 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
   al(&m->cand_i, ncand * 4);
   al(&m->colws, (size_t)(B / kColChunk + 1) * std::max(m->Spad, std::max(H1, H2)) * 4);
   al(&m->splitws, (size_t)kSplitK * B * H2 * 4);
+  al(&m->stats, (size_t)((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcListsPerTile * B * 2 * 4);
+  al(&m->zlab, B * 4);
+  al(&m->row_m, B * 4);
+  al(&m->row_inv, B * 4);
   if (e != cudaSuccess) {
     free_model(m);
     return hp::cuda_fail(e, "hp_mlp_create: device allocation");
@@ -793,8 +841,7 @@ extern "C" int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t*
   const int rows = round_up(n, 32);
   cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
   cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-  int rc = forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
-  if (rc == HP_OK) rc = backward(m, n, rows, st);
+  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
   if (rc != HP_OK) return rc;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_gradients: launch");
@@ -827,8 +874,7 @@ extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t
   const int rows = round_up(n, 32);
   cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
   cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-  int rc = forward(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
-  if (rc == HP_OK) rc = backward(m, n, rows, st);
+  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
   if (rc != HP_OK) return rc;
   m->steps++;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;

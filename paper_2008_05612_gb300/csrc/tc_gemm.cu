@@ -44,7 +44,7 @@ struct Shape {
   static constexpr int kThreads = 64 + 32 * kEpiWarps;
   static constexpr int kColsPerWarp = TN / (kEpiWarps / 4);
   static constexpr int kStages = 3;
-  static constexpr int kAreaFloats = KT > 0 ? SX_FLOATS + kColsPerWarp : SQ_FLOATS;
+  static constexpr int kAreaFloats = KT > 0 ? SX_FLOATS + kColsPerWarp : KT < 0 ? SQ_FLOATS + kColsPerWarp : SQ_FLOATS;
   static constexpr int kSmem = kStages * STAGE_BYTES + kEpiWarps * kAreaFloats * 4 + 1024;
 };
 constexpr uint32_t SPIN_LIMIT = 1u << 24;
@@ -257,13 +257,13 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
     constexpr int CW = Shape<KT>::kColsPerWarp;
     const int cbeg = h * CW, cend = cbeg + CW;
     float* area = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES) + (warp - 2) * Shape<KT>::kAreaFloats;
-    float* bsm = area + SX_FLOATS;  // top-k mode: this warp's biases of the current tile
+    float* bsm = area + (KT > 0 ? SX_FLOATS : SQ_FLOATS);  // top-k / softmax modes: this warp's biases of the tile
     const TcEpilogue& ep = p.ep;
     // top-k mode: biases of the next tile, one column per lane and 32-column chunk, loaded a
     // whole tile ahead of use
-    float bnext[KT > 0 ? CW / 32 : 1];
+    float bnext[KT != 0 ? CW / 32 : 1];
     auto fetch_bias = [&](int n0) {
-      if constexpr (KT > 0) {
+      if constexpr (KT != 0) {
 #pragma unroll
         for (int i = 0; i < CW / 32; i++) {
           const int c = n0 + cbeg + 32 * i + lane;
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         }
       }
     };
-    if (KT > 0 && (int)blockIdx.x < p.units) fetch_bias(unit_of(p, blockIdx.x).nb * TN);
+    if (KT != 0 && (int)blockIdx.x < p.units) fetch_bias(unit_of(p, blockIdx.x).nb * TN);
     uint32_t tl = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
@@ -288,6 +288,18 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         bi[j] = INT_MAX;
       }
       bool seeded = false;
+      // softmax modes: this thread's row, its label and (statistics) running max / sum or
+      // (gradient) the row's max and 1 / sum
+      const int my_row = rbase + lane;
+      const int lab = (KT < 0 && my_row < p.M && ep.labels) ? ep.labels[my_row] : -1;
+      float rm = -INFINITY, rs = 0.f, zl = 0.f;
+      bool have_zl = false;
+      if constexpr (KT == -2) {
+        if (my_row < p.M) {
+          rm = ep.row_m[my_row];
+          rs = ep.row_inv[my_row];
+        }
+      }
       for (int tn = w.nb; tn < w.ne; tn++, tl++) {
         const uint32_t a = tl & 1, ar = tl >> 1;
         if (!wait_or_abort(&tmem_full[a], ar & 1, abort_flag, err)) {
@@ -296,7 +308,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int n0 = tn * TN;
-        if constexpr (KT > 0) {
+        if constexpr (KT != 0) {
           __syncwarp();
 #pragma unroll
           for (int i = 0; i < CW / 32; i++) bsm[32 * i + lane] = bnext[i];
@@ -326,6 +338,55 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
               }
             }
             __syncwarp();
+          } else if constexpr (KT < 0) {
+            const int cmax = min(32, p.N - (n0 + c0));
+            const int cbase = n0 + c0;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              const float4 b4 = *reinterpret_cast<const float4*>(bsm + (c0 - cbeg) + j);
+              v[j] = __float_as_uint(__uint_as_float(v[j]) + b4.x);
+              v[j + 1] = __float_as_uint(__uint_as_float(v[j + 1]) + b4.y);
+              v[j + 2] = __float_as_uint(__uint_as_float(v[j + 2]) + b4.z);
+              v[j + 3] = __float_as_uint(__uint_as_float(v[j + 3]) + b4.w);
+            }
+            if constexpr (KT == -1) {
+              // running max and sum of exponentials over the chunk's valid columns
+              float cm = -INFINITY;
+#pragma unroll
+              for (int j = 0; j < 32; j++)
+                if (j < cmax) cm = fmaxf(cm, __uint_as_float(v[j]));
+              const float nm = fmaxf(rm, cm);
+              float acc = 0.f;
+#pragma unroll
+              for (int j = 0; j < 32; j++)
+                if (j < cmax) acc += __expf(__uint_as_float(v[j]) - nm);
+              rs = (rm == -INFINITY ? 0.f : rs * __expf(rm - nm)) + acc;
+              rm = nm;
+              if (lab >= cbase && lab < cbase + cmax) {  // once per row: pick the label's logit
+#pragma unroll
+                for (int j = 0; j < 32; j++) area[lane * 33 + j] = __uint_as_float(v[j]);
+                zl = area[lane * 33 + (lab - cbase)];
+                have_zl = true;
+              }
+            } else {
+              // dz = (softmax - onehot) * scale; transposed stores straight from the row layout
+              // (lanes = 32 consecutive rows of one column), row-major ones through the square
+#pragma unroll
+              for (int j = 0; j < 32; j++) {
+                const int col = cbase + j;
+                float d = 0.f;
+                if (lab >= 0 && j < cmax) d = (__expf(__uint_as_float(v[j]) - rm) * rs - (col == lab ? 1.f : 0.f)) * ep.scale;
+                area[lane * 33 + j] = d;
+                if (j < cmax && my_row < p.M) ep.dzt[(size_t)col * ep.ldzt + my_row] = __float2bfloat16(d);
+              }
+              __syncwarp();
+              if (lane < cmax) {
+                const int rmax = min(32, p.M - rbase);
+                for (int r = 0; r < rmax; r++)
+                  ep.dz[(size_t)(rbase + r) * ep.ldz + cbase + lane] = __float2bfloat16(area[r * 33 + lane]);
+              }
+              __syncwarp();
+            }
           } else {
             // 1. bias-added logits of the chunk
             const int cmax = min(32, p.N - (n0 + c0));
@@ -401,6 +462,13 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(&tmem_empty[a])) : "memory");
+      }
+      if constexpr (KT == -1) {
+        if (ok && my_row < p.M) {
+          const size_t l = (size_t)(w.r * kTcListsPerTile + h);
+          *reinterpret_cast<float2*>(ep.stats + 2 * (l * p.M + my_row)) = make_float2(rm, rs);
+          if (have_zl) ep.zlab[my_row] = zl;
+        }
       }
       if constexpr (KT > 0) {
         const int row = rbase + lane;
@@ -487,6 +555,25 @@ __global__ void topk_merge_kernel(const float* __restrict__ cv, const int32_t* _
   }
 }
 
+// Per row: combine the (max, sum of exp) pairs of all lists.
+__global__ void softmax_finish_kernel(const float* __restrict__ stats, int lists, int rows, const int32_t* __restrict__ labels,
+                                      const float* __restrict__ zlab, float* __restrict__ row_m, float* __restrict__ row_inv,
+                                      float* __restrict__ loss) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  float m = -INFINITY, s = 0.f;
+  for (int l = 0; l < lists; l++) {
+    const float2 q = *reinterpret_cast<const float2*>(stats + 2 * ((size_t)l * rows + r));
+    if (q.x == -INFINITY) continue;
+    const float nm = fmaxf(m, q.x);
+    s = (m == -INFINITY ? 0.f : s * __expf(m - nm)) + q.y * __expf(q.x - nm);
+    m = nm;
+  }
+  row_m[r] = m;
+  row_inv[r] = 1.f / s;
+  if (labels && labels[r] >= 0) atomicAdd(loss, logf(s) + m - zlab[r]);
+}
+
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                                 const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -547,8 +634,13 @@ int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
   if (M < 1 || N < 1 || K < 1 || lda % 8 || ldb % 8 || lda < K || ldb < K ||
       (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) % 16)
     return fail(HP_EINVAL, "tc_gemm: bad shape, stride or alignment");
-  if (ep.kt && ((ep.kt != 4 && ep.kt != 8 && ep.kt != 16) || !ep.cand_v || !ep.cand_i))
+  if (ep.kt > 0 && ((ep.kt != 4 && ep.kt != 8 && ep.kt != 16) || !ep.cand_v || !ep.cand_i))
     return fail(HP_EINVAL, "tc_gemm: top-k mode needs kt in {4, 8, 16} and candidate buffers");
+  if (ep.kt == -1 && (!ep.stats || !ep.zlab || !ep.labels))
+    return fail(HP_EINVAL, "tc_gemm: row-statistics mode needs stats, zlab and labels");
+  if (ep.kt == -2 && (!ep.row_m || !ep.row_inv || !ep.labels || !ep.dz || !ep.dzt || (ep.ldz | ep.ldzt) <= 0))
+    return fail(HP_EINVAL, "tc_gemm: gradient mode needs row statistics, labels and both outputs");
+  if (ep.kt < -2) return fail(HP_EINVAL, "tc_gemm: unknown epilogue mode");
   CUtensorMap ma, mb;
   int rc = make_map(&ma, A, M, K, lda, TM);
   if (rc == HP_OK) rc = make_map(&mb, B, N, K, ldb, TN);
@@ -557,15 +649,22 @@ int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
   if (ep.ksplit < 1 || ep.ksplit > nk || (ep.ksplit > 1 && (ep.kt || ep.Cb || ep.bias || ep.relu || !ep.Cf)))
     return fail(HP_EINVAL, "tc_gemm: split-K needs store mode with an fp32 output only and at most one slice per K chunk");
   Params p{M, N, K, (M + TM - 1) / TM, (N + TN - 1) / TN, 0, 0, ep.ksplit, ep, err};
-  p.nr = ep.kt ? tc_topk_lists(M, N) / kTcListsPerTile : p.nt;
+  p.nr = (ep.kt > 0 || ep.kt == -1) ? tc_topk_lists(M, N) / kTcListsPerTile : p.nt;
   p.units = p.mt * p.nr * p.ksplit;
   switch (ep.kt) {
     case 0: launch<0>(ma, mb, p, st); break;
+    case -1: launch<-1>(ma, mb, p, st); break;
+    case -2: launch<-2>(ma, mb, p, st); break;
     case 4: launch<4>(ma, mb, p, st); break;
     case 8: launch<8>(ma, mb, p, st); break;
     default: launch<16>(ma, mb, p, st); break;
   }
   return HP_OK;
+}
+
+void tc_softmax_finish(const float* stats, int lists, int rows, const int32_t* labels, const float* zlab, float* row_m,
+                       float* row_inv, float* loss, cudaStream_t st) {
+  softmax_finish_kernel<<<(rows + 255) / 256, 256, 0, st>>>(stats, lists, rows, labels, zlab, row_m, row_inv, loss);
 }
 
 void tc_topk_merge(const float* cand_v, const int32_t* cand_i, int tiles, int rows, int kt, int k, int S, int32_t* out,

@@ -29,6 +29,24 @@ struct TcEpilogue {
   int kt = 0;
   float* cand_v = nullptr;
   int32_t* cand_i = nullptr;
+  // softmax modes over the columns of each row (the proposal's training step; bias added, rows
+  // with label -1 ignored):
+  //   kt = -1 (row statistics): per row and column list l (as in top-k mode) the running
+  //     maximum m and sum of exp(x - m) go to stats[2 (l M + r) + {0, 1}]; the logit at the row's
+  //     label goes to zlab[r];
+  //   kt = -2 (cross-entropy gradient): with row_m / row_inv the row's maximum and 1 / sum,
+  //     dz = (exp(x - m) / sum - [column == label]) * scale, zero for label -1, stored as bf16 both
+  //     row-major (dz, row stride ldz) and transposed (dzt, row stride ldzt)
+  const int32_t* labels = nullptr;
+  float* stats = nullptr;
+  float* zlab = nullptr;
+  const float* row_m = nullptr;
+  const float* row_inv = nullptr;
+  float scale = 1.f;
+  __nv_bfloat16* dz = nullptr;
+  int ldz = 0;
+  __nv_bfloat16* dzt = nullptr;
+  int ldzt = 0;
   // split-K (store mode, fp32 output only, no bias / ReLU): the K chunks are cut into ksplit
   // contiguous slices computed by different CTAs; slice j's partial product goes to
   // Cf + j * split_stride, and the caller sums the slices
@@ -43,6 +61,11 @@ int tc_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, in
 
 // Number of candidate lists per row that top-k mode writes (at most 2 ceil(N / 256)).
 int tc_topk_lists(int M, int N);
+
+// Combine the row-statistics lists of kt = -1 mode: row_m[r], row_inv[r] = 1 / sum, and for
+// labelled rows log(sum) + m - zlab[r] added to *loss.
+void tc_softmax_finish(const float* stats, int lists, int rows, const int32_t* labels, const float* zlab, float* row_m,
+                       float* row_inv, float* loss, cudaStream_t st);
 
 // Per row, the k <= kt best of the candidates tc_gemm wrote for `tiles` column lists (ties toward
 // the lower index); out[r * k + j], -1 for a missing entry or an index >= S.
