@@ -144,19 +144,39 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
           if (orig[u] >= 0) take(10 * A[u] + 3 * B[u], orig[u]);
       }
     }
+    // the next 32 groups' count planes and member ranges are loaded while the current ones are
+    // tested (the step is short and latency-bound otherwise)
+    uint32_t cw[6] = {0, 0, 0, 0, 0, 0};
+    int cb0 = 0, cb1 = 0;
+    auto fetch = [&](int g0, uint32_t (&c)[6], int& b0, int& b1) {
+      const int gi = g0 + lane;
+      if (gi < p.ngroups) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) c[k] = __ldg(p.gcnt + (size_t)k * p.gpad + gi);
+        b0 = __ldg(p.gbeg + gi);
+        b1 = __ldg(p.gbeg + gi + 1);
+      }
+    };
+    if (cand >= 0) fetch(0, cw, cb0, cb1);
     for (int g0 = 0; cand >= 0 && g0 < p.ngroups; g0 += 32) {
+      uint32_t nw[6] = {0, 0, 0, 0, 0, 0};
+      int nb0 = 0, nb1 = 0;
+      if (g0 + 32 < p.ngroups) fetch(g0 + 32, nw, nb0, nb1);
       // lane l: group g0 + l, its A and bound
       const int gi = g0 + lane;
-      int A = 0, n = 0, beg = 0;
+      int A = 0, n = 0;
+      const int beg = cb0;
       if (gi < p.ngroups) {
-        const uint32_t* c = p.gcnt + gi;
-        const size_t w = (size_t)p.gpad;
-        A = (__popc(e & __ldg(c)) + __popc(o & __ldg(c + 3 * w))) + 2 * (__popc(e & __ldg(c + w)) + __popc(o & __ldg(c + 4 * w))) +
-            4 * (__popc(e & __ldg(c + 2 * w)) + __popc(o & __ldg(c + 5 * w)));
-        beg = __ldg(p.gbeg + gi);
+        A = (__popc(e & cw[0]) + __popc(o & cw[3])) + 2 * (__popc(e & cw[1]) + __popc(o & cw[4])) +
+            4 * (__popc(e & cw[2]) + __popc(o & cw[5]));
         n_bound++;
-        if (cand < 0 || upper(A, p.C) >= cand) n = __ldg(p.gbeg + gi + 1) - beg;
+        if (upper(A, p.C) >= cand) n = cb1 - cb0;
       }
+#pragma unroll
+      for (int k = 0; k < 6; k++) cw[k] = nw[k];
+      cb0 = nb0;
+      cb1 = nb1;
+      if (!__any_sync(0xFFFFFFFFu, n > 0)) continue;  // no group of this step survives
       // inclusive prefix sum of the surviving members over the lanes
       int incl = n;
 #pragma unroll
