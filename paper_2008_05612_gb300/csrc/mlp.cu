@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -410,6 +411,18 @@ __global__ void splitk_relu_backward(const float* __restrict__ part, int splits,
   }
 }
 
+// out[pos, :] = in[perm[pos], :] (rows of H bf16, H a multiple of 8) and bout[pos] = bias[perm[pos]]
+__global__ void gather_rows(const bf16* __restrict__ in, const float* __restrict__ bias, const int32_t* __restrict__ perm,
+                            int S, int H, bf16* __restrict__ out, float* __restrict__ bout) {
+  const size_t chunks = (size_t)H / 8, n = (size_t)S * chunks;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t pos = i / chunks, c = i % chunks;
+    const int src = perm[pos];
+    reinterpret_cast<uint4*>(out + pos * H)[c] = reinterpret_cast<const uint4*>(in + (size_t)src * H)[c];
+    if (c == 0) bout[pos] = bias[src];
+  }
+}
+
 // dA = dH * (H > 0), fp32 in, bf16 out
 __global__ void relu_backward(const float* __restrict__ dH, const bf16* __restrict__ H, bf16* __restrict__ dA, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -541,6 +554,12 @@ struct hp_mlp {
   // training with the softmax in the output layer's epilogue: per-list row statistics, the
   // label logit, and each row's max and 1 / sum
   float *stats = nullptr, *zlab = nullptr, *row_m = nullptr, *row_inv = nullptr;
+  // the proposal's output layer in a scattered class order: neighbouring classes in canonical
+  // order are similar folds with similar logits, which would make the fused top-k's running
+  // threshold climb slowly along a row; perm[pos] = class at position pos
+  int32_t* perm = nullptr;
+  bf16* w3p = nullptr;
+  float* b3p = nullptr;
   int steps = 0;
 };
 
@@ -701,6 +720,7 @@ void refresh_copies(hp_mlp* m, cudaStream_t st) {
   cast_bf16<<<grid_for(m->n[4]), 256, 0, st>>>(m->w[4], m->w3b, m->n[4]);
   transpose(m->w2b, m->H1, m->H2, m->H1, m->w2t, m->H2, m->H2, st);
   transpose(m->w3b, m->H2, m->S, m->H2, m->w3t, m->Spad, m->Spad, st);
+  gather_rows<<<grid_for((size_t)m->S * (m->H2 / 8)), 256, 0, st>>>(m->w3b, m->w[5], m->perm, m->S, m->H2, m->w3p, m->b3p);
 }
 
 void free_model(hp_mlp* m) {
@@ -713,7 +733,7 @@ void free_model(hp_mlp* m) {
   }
   void* ptrs[] = {m->w1b, m->w2b, m->w3b, m->w2t, m->w3t, m->X,  m->XT,  m->Hb1, m->Hb2,  m->H1T,  m->H2T,
                   m->Z,   m->dHf, m->loss, m->dZ,  m->dZT, m->dA2, m->dA2T, m->dA1, m->dA1T, m->labels, m->tc_err, m->cand_v, m->cand_i,
-                  m->colws, m->splitws, m->stats, m->zlab, m->row_m, m->row_inv};
+                  m->colws, m->splitws, m->stats, m->zlab, m->row_m, m->row_inv, m->perm, m->w3p, m->b3p};
   for (void* p : ptrs) cudaFree(p);
   delete m;
 }
@@ -788,6 +808,9 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
   al(&m->zlab, B * 4);
   al(&m->row_m, B * 4);
   al(&m->row_inv, B * 4);
+  al(&m->perm, (size_t)S * 4);
+  al(&m->w3p, m->n[4] * 2);
+  al(&m->b3p, (size_t)S * 4);
   if (e != cudaSuccess) {
     free_model(m);
     return hp::cuda_fail(e, "hp_mlp_create: device allocation");
@@ -801,6 +824,18 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
   if (e != cudaSuccess) {
     free_model(m);
     return hp::cuda_fail(e, "hp_mlp_create: upload");
+  }
+  {
+    // multiplicative scatter pos -> (pos * a) mod S with a near 0.618 S and coprime to S
+    long long a = std::max(1ll, (long long)(0.6180339887 * S));
+    while (std::gcd(a, (long long)S) != 1) a++;
+    std::vector<int32_t> perm(S);
+    for (int pos = 0; pos < S; pos++) perm[pos] = (int32_t)(((long long)pos * a) % S);
+    e = cudaMemcpy(m->perm, perm.data(), (size_t)S * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      free_model(m);
+      return hp::cuda_fail(e, "hp_mlp_create: upload");
+    }
   }
   refresh_copies(m, nullptr);
   e = cudaDeviceSynchronize();
@@ -908,11 +943,12 @@ extern "C" int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t 
       // output layer with the top-k fused into the GEMM epilogue: logits never reach memory
       int rc = forward_hidden(m, ids, nb, rows, st);
       hp::TcEpilogue ep;
-      ep.bias = m->w[5];
+      ep.bias = m->b3p;
       ep.kt = k <= 4 ? 4 : k <= 8 ? 8 : 16;
       ep.cand_v = m->cand_v;
       ep.cand_i = m->cand_i;
-      if (rc == HP_OK) rc = hp::tc_gemm(m->Hb2, m->H2, m->w3b, m->H2, nb, m->S, m->H2, ep, m->tc_err, st);
+      ep.col_id = m->perm;
+      if (rc == HP_OK) rc = hp::tc_gemm(m->Hb2, m->H2, m->w3p, m->H2, nb, m->S, m->H2, ep, m->tc_err, st);
       if (rc != HP_OK) return rc;
       hp::tc_topk_merge(m->cand_v, m->cand_i, hp::tc_topk_lists(nb, m->S), nb, ep.kt, k, m->S, d_top + off * k, st);
     } else {

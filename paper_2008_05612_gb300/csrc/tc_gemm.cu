@@ -278,8 +278,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
       const Unit w = unit_of(p, u);
       const int rbase = w.m0 + q * 32;  // first row of this warp
       // top-k mode: one running list per row over this warp's columns of all tiles of the unit,
-      // ordered by (value descending, index ascending); columns arrive in increasing order, so a
-      // value equal to the list's last never enters
+      // ordered by (value descending, id ascending)
       float bv[KT > 0 ? KT : 1];
       int bi[KT > 0 ? KT : 1];
 #pragma unroll
@@ -398,10 +397,11 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
               v[j + 2] = __float_as_uint(__uint_as_float(v[j + 2]) + b4.z);
               v[j + 3] = __float_as_uint(__uint_as_float(v[j + 3]) + b4.w);
             }
-            // 2. the columns that can enter: above the list's current last or, for the list's
-            //    first full chunk, at least the smallest of KT group maxima (KT columns reach it,
-            //    so nothing below it is among the KT best)
-            float thr = bv[KT - 1];
+            // 2. the columns that can enter: at least the list's current last (equal values are
+            //    settled on their ids below) or, for the list's first full chunk, at least the
+            //    smallest of KT group maxima (KT columns reach it, so nothing below it is among
+            //    the KT best)
+            float thr = nextafterf(bv[KT - 1], -INFINITY);  // x > thr  <=>  x >= last
             if (!seeded && cmax == 32) {
               constexpr int G = 32 / KT;
               float t0 = INFINITY;
@@ -441,8 +441,8 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
                   const int j = __ffs(mask) - 1;
                   mask &= mask - 1;
                   float cv = area[lane * 32 + (((j >> 2) ^ (lane & 7)) << 2) + (j & 3)];
-                  if (cv > bv[KT - 1]) {
-                    int ci = n0 + c0 + j;
+                  int ci = ep.col_id ? __ldg(ep.col_id + n0 + c0 + j) : n0 + c0 + j;
+                  if (cv > bv[KT - 1] || (cv == bv[KT - 1] && ci < bi[KT - 1])) {
 #pragma unroll
                     for (int e = 0; e < KT; e++) {
                       const bool take = cv > bv[e] || (cv == bv[e] && ci < bi[e]);

@@ -29,6 +29,8 @@ struct TcEpilogue {
   int kt = 0;
   float* cand_v = nullptr;
   int32_t* cand_i = nullptr;
+  // top-k mode: if set, column c is reported (and ordered on ties) as col_id[c] instead of c
+  const int32_t* col_id = nullptr;
   // softmax modes over the columns of each row (the proposal's training step; bias added, rows
   // with label -1 ignored):
   //   kt = -1 (row statistics): per row and column list l (as in top-k mode) the running
