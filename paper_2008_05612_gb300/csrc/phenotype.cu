@@ -298,11 +298,6 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       o = odd_bits(bd.g_base) | (uint32_t)(local & ((1ull << bd.no_free) - 1));
       chunk = (uint32_t)(local >> bd.no_free);
     }
-    // reversal mirror of this item's ids (only for non-palindromic odd patterns); when every free
-    // even residue is a role of this CTA, the mirrored ids are written in a second, coalesced pass
-    const uint32_t o_rev = bd.otab ? (__brev(o) >> (32 - bd.no_free)) : o;  // no_free >= 1 with a table
-    const bool mirror = bd.otab != nullptr && o_rev != o;
-    const bool mirror_gather = mirror && bd.ne_free == bd.nroles;
     const int nroles = (int)bd.nroles;
     const uint32_t ehigh = even_bits(bd.g_base) | (chunk << nroles);
     const uint32_t role_mask = (1u << nroles) - 1u;
@@ -487,6 +482,13 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       }
     }
     if (s_abort) break;
+
+    // reversal mirror of this item's ids (only for non-palindromic odd patterns); when every free
+    // even residue is a role of this CTA, the mirrored ids are written in a second, coalesced pass
+    // (computed here, not at the top of the item, so that nothing extra stays live through pass 1)
+    const uint32_t o_rev = bd.otab ? (__brev(o) >> (32 - bd.no_free)) : o;  // no_free >= 1 with a table
+    const bool mirror = bd.otab != nullptr && o_rev != o;
+    const bool mirror_gather = mirror && bd.ne_free == bd.nroles;
 
     // ================= write the two sequences of each packed register (ids differ in bit 0)
     for (int v = 0; v < P; v++) {
