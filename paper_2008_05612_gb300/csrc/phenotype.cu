@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       }
       const uint32_t* cbuf = coefbuf + b * T * CSTRIDE;
       auto consume = [&](int s0, int s1) {
-#pragma unroll 2
+#pragma unroll 8
         for (int s = s0; s < s1; s++) {
           const uint32_t* cs = cbuf + s * CSTRIDE;
           uint32_t tpv[K::TP_WORDS];
