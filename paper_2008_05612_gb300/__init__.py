@@ -257,7 +257,7 @@ class BatchPlan:
 def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, stream=None):
     """Phenotypes of arbitrary ids (hp_sequence_scan); cand: int32 [n, k] candidate conformations or None.
     Returns phen (and aux if requested); counters (int64[2] CUDA tensor) accumulates
-    (exact evaluations, bound evaluations)."""
+    (conformations evaluated exactly, contact-count group bounds evaluated)."""
     import torch
 
     n = ids.numel()
