@@ -64,6 +64,8 @@ def _load():
         lib.or_lower_bound.argtypes = [vp, ctypes.c_uint64, i32]
         lib.or_phenotypes.restype = ctypes.c_int
         lib.or_phenotypes.argtypes = [vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int]
+        lib.or_phenotypes_gaps.restype = ctypes.c_int
+        lib.or_phenotypes_gaps.argtypes = [vp, vp, i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int]
         lib.or_designability.argtypes = [vp, ctypes.c_uint64, i32, vp]
         lib.or_robustness.argtypes = [vp, ctypes.c_int, i32, vp, vp]
         lib.or_neighbourhood.argtypes = [vp, ctypes.c_int, i32, i32, vp]
@@ -127,20 +129,28 @@ class Box:
     def lower_bound(self, g: int, s: int) -> int:
         return int(_load().or_lower_bound(self._h, int(g), int(s)))
 
-    def phenotypes(self, seqs, reading: int = READING_B, gap: int = 1, nthreads: int | None = None, aux: bool = False):
+    def phenotypes(self, seqs, reading: int = READING_B, gap: int = 1, nthreads: int | None = None, aux: bool = False,
+                   gaps: bool = False):
+        """Phenotypes of the ids (Section 2.1 with energy-gap threshold `gap`); with aux, also the class of
+        the lowest-index minimiser; with gaps, also E2 - E1 (second-lowest energy counted with
+        multiplicity minus the lowest; INT32_MAX for a single competitor).  Returns phen, then aux and
+        gaps in that order when requested."""
         seqs = np.ascontiguousarray(np.asarray(seqs, dtype=np.uint64))
         n = seqs.shape[0]
         phen = np.zeros(n, dtype=np.int32)
         auxa = np.zeros(n, dtype=np.int32) if aux else None
+        gapa = np.zeros(n, dtype=np.int32) if gaps else None
         nt = nthreads or min(os.cpu_count() or 1, 64)
-        rc = _load().or_phenotypes(self._h, _ptr(seqs), n, int(reading), int(gap), _ptr(phen),
-                                   _ptr(auxa) if aux else None, int(nt))
+        rc = _load().or_phenotypes_gaps(self._h, _ptr(seqs), n, int(reading), int(gap), _ptr(phen),
+                                        _ptr(auxa) if aux else None, _ptr(gapa) if gaps else None, int(nt))
         if rc != 0:
             raise ValueError("oracle rejected the phenotype request")
-        return (phen, auxa) if aux else phen
+        out = (phen,) + ((auxa,) if aux else ()) + ((gapa,) if gaps else ())
+        return out if len(out) > 1 else phen
 
-    def full_map(self, reading: int = READING_B, gap: int = 1, nthreads: int | None = None, aux: bool = False):
-        return self.phenotypes(np.arange(1 << self.N, dtype=np.uint64), reading, gap, nthreads, aux)
+    def full_map(self, reading: int = READING_B, gap: int = 1, nthreads: int | None = None, aux: bool = False,
+                 gaps: bool = False):
+        return self.phenotypes(np.arange(1 << self.N, dtype=np.uint64), reading, gap, nthreads, aux, gaps)
 
 
 def designability(phen: np.ndarray, S: int) -> np.ndarray:

@@ -355,8 +355,11 @@ int or_lower_bound(const or_box *b, uint64_t g, int32_t s) {
   return -10 * A - 3 * Bmax;
 }
 
-/* ground state of one sequence under the chosen reading */
-static void ground_state(const or_box *b, uint64_t g, int reading, int gap, int32_t *phen, int32_t *aux) {
+/* ground state of one sequence under the chosen reading; *gap_out (optional)
+ * receives e2 - e1, the energy difference the Appendix C kernel returns with
+ * its sign flipped, or INT32_MAX when there is a single competitor */
+static void ground_state(const or_box *b, uint64_t g, int reading, int gap, int32_t *phen, int32_t *aux,
+                         int32_t *gap_out) {
   int e1 = 1 << 30, e2 = 1 << 30;   /* lowest and second-lowest (with multiplicity) */
   int32_t first = -1;               /* lowest-index conformation at e1 */
   int e2_other = 1 << 30;           /* reading C: lowest energy of any other class */
@@ -385,8 +388,10 @@ static void ground_state(const or_box *b, uint64_t g, int reading, int gap, int3
   if (aux) *aux = cls;
   if (b->S_dir == 1 || (reading == 2 && b->S == 1)) {
     *phen = cls; /* a single competitor is always the unique minimum */
+    if (gap_out) *gap_out = INT32_MAX;
     return;
   }
+  if (gap_out) *gap_out = e2 - e1;
   *phen = (e2 - e1 >= gap) ? cls : -1;
 }
 
@@ -395,21 +400,24 @@ typedef struct {
   const uint64_t *seqs;
   int64_t lo, hi;
   int reading, gap;
-  int32_t *phen, *aux;
+  int32_t *phen, *aux, *gaps;
 } gs_job;
 
 static void *gs_worker(void *arg) {
   gs_job *j = (gs_job *)arg;
   for (int64_t i = j->lo; i < j->hi; i++)
-    ground_state(j->b, j->seqs[i], j->reading, j->gap, &j->phen[i], j->aux ? &j->aux[i] : NULL);
+    ground_state(j->b, j->seqs[i], j->reading, j->gap, &j->phen[i], j->aux ? &j->aux[i] : NULL,
+                 j->gaps ? &j->gaps[i] : NULL);
   return NULL;
 }
 
 /* Phenotype of each listed sequence id.  reading: 0 = A, 1 = B, 2 = C.
  * aux (optional) receives the class of the lowest-index conformation at the
- * minimum energy, tied or not. */
-int or_phenotypes(const or_box *b, const uint64_t *seqs, int64_t n, int reading, int gap, int32_t *phen,
-                  int32_t *aux, int nthreads) {
+ * minimum energy, tied or not; gaps (optional) the difference between the
+ * second-lowest energy (with multiplicity: 0 when the minimum is tied) and
+ * the lowest, INT32_MAX for a single competitor. */
+int or_phenotypes_gaps(const or_box *b, const uint64_t *seqs, int64_t n, int reading, int gap, int32_t *phen,
+                       int32_t *aux, int32_t *gaps, int nthreads) {
   if (reading < 0 || reading > 2 || gap < 1 || b->S_dir < 1) return -1;
   for (int64_t i = 0; i < n; i++)
     if (b->N < 64 && (seqs[i] >> b->N) != 0) return -1;
@@ -426,10 +434,16 @@ int or_phenotypes(const or_box *b, const uint64_t *seqs, int64_t n, int reading,
     jobs[t].gap = gap;
     jobs[t].phen = phen;
     jobs[t].aux = aux;
+    jobs[t].gaps = gaps;
     pthread_create(&th[t], NULL, gs_worker, &jobs[t]);
   }
   for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
   return 0;
+}
+
+int or_phenotypes(const or_box *b, const uint64_t *seqs, int64_t n, int reading, int gap, int32_t *phen,
+                  int32_t *aux, int nthreads) {
+  return or_phenotypes_gaps(b, seqs, n, reading, gap, phen, aux, NULL, nthreads);
 }
 
 /* --------------------------------------------------------------- reductions */

@@ -119,3 +119,18 @@ def phenotype_map(dims):
         idx = [k for k, e in enumerate(es) if e == m]
         out[g] = cls[idx[0]] if len(idx) == 1 else -1
     return out, S
+
+
+def gap_map(dims):
+    """Per genotype: class of the lowest-index minimiser and E2 - E1 (second-lowest energy counted
+    with multiplicity minus the lowest; None for a single conformation)."""
+    order, cls, S = library(dims)
+    N = len(order[0])
+    first, gaps = [], []
+    for g in range(1 << N):
+        es = [energy(c, g, dims) for c in order]
+        m = min(es)
+        first.append(cls[es.index(m)])
+        srt = sorted(es)
+        gaps.append(srt[1] - srt[0] if len(srt) > 1 else None)
+    return first, gaps, S

@@ -43,6 +43,12 @@ def test_2x3_hand_worked_readings(obox):
     assert B.tolist() == [k, -1, k, -1, -1]
     assert C.tolist() == [k, k, k, -1, -1]
     assert A[2] == k and A[3] == -1 and A[4] == -1
+    # energy gaps E2 - E1 under B (Appendix C returns their negatives): -20 vs -10, a tie at -33,
+    # -20 vs -10, and two all-equal rows; a gap of 10 folds up to threshold 10 and not at 11
+    _, gaps = b.phenotypes(seqs, gaps=True)
+    assert gaps.tolist() == [10, 0, 10, 0, 0]
+    assert b.phenotypes(seqs, gap=10).tolist() == [k, -1, k, -1, -1]
+    assert b.phenotypes(seqs, gap=11).tolist() == [-1, -1, -1, -1, -1]
 
 
 @pytest.mark.parametrize("dims", [(4, 4), (2, 4), (3, 4)])
@@ -68,6 +74,27 @@ def test_gap_threshold_monotone(obox):
         assert ((mT == -1) | (mT == m1)).all()
         assert (mT >= 0).sum() <= (m1 >= 0).sum()
         m1 = mT
+
+
+@pytest.mark.parametrize("dims", [(2, 3), (3, 3), (2, 2, 2)])
+def test_gaps_and_thresholds_equal_brute_force(obox, dims):
+    """E2 - E1 and the phenotype at energy-gap thresholds T > 1 (Section 2.1; Appendix C keeps the
+    lowest and second-lowest energy) against the brute force: a genotype folds iff E2 - E1 >= T."""
+    b = obox(dims)
+    first, want_gaps, S = _brute.gap_map(dims)
+    phen, aux, gaps = b.full_map(aux=True, gaps=True)
+    assert aux.tolist() == first
+    assert gaps.tolist() == want_gaps
+    g = np.array(want_gaps)
+    for T in (1, 3, 10, 13, 20, 23, 33):
+        want = np.where(g >= T, np.array(first), -1)
+        np.testing.assert_array_equal(b.full_map(gap=T), want)
+
+
+def test_single_conformation_gap_is_unbounded(obox):
+    b = obox((2, 2))
+    phen, gaps = b.full_map(gap=1000, gaps=True)
+    assert (phen == 0).all() and (gaps == np.iinfo(np.int32).max).all()
 
 
 def test_aux_is_lowest_index_minimiser(obox):
