@@ -70,10 +70,14 @@ int hp_structs_export(const hp_structs* s, uint8_t* coords, uint8_t* contacts, i
 void hp_structs_free(hp_structs* s);
 
 /* Ground-state phenotype of every sequence id in [seq_begin, seq_begin +
- * seq_count) (Section 2.1; Appendix C kernel semantics with threshold 1).
- *   gap_threshold: minimum energy gap between the lowest and second-lowest
- *                  conformation for a sequence to fold; only 1 (strict
- *                  uniqueness) is implemented, others give HP_EUNSUPPORTED.
+ * seq_count) (Section 2.1; Appendix C kernel semantics).
+ *   gap_threshold: minimum energy gap E2 - E1 (x 10 units, E2 the second-
+ *                  lowest energy counted with multiplicity) for a sequence to
+ *                  fold; 1 = strict uniqueness (the paper's value) runs the
+ *                  tiled map kernel; values in [2, 2^20] run the per-sequence
+ *                  scan of hp_sequence_scan_gap over the range (exact, slower,
+ *                  stream-ordered without synchronising); < 1 or > 2^20 give
+ *                  HP_EINVAL.
  *   d_phen:        device int32[seq_count]; d_phen[k] = phenotype of
  *                  seq_begin + k: class id, or -1.
  *   d_argmin_aux:  optional device int32[seq_count] (NULL to skip): class of
@@ -154,6 +158,23 @@ void hp_batch_plan_free(hp_batch_plan* plan);
  * its sampled kernel (Appendix C). */
 int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand, int32_t k,
                      int32_t* d_phen, int32_t* d_aux, uint64_t* d_counters, void* stream);
+
+/* hp_sequence_scan at an energy-gap threshold, with the gap itself (the
+ * Appendix C kernel returns the lowest energy's fold and E1 - E2).  A sequence
+ * folds iff E2 - E1 >= gap_threshold (Section 2.1), E2 the second-lowest
+ * energy counted with multiplicity (0 gap when the minimum is tied).  Pruning
+ * skips a group only when its bound lies gap_threshold or more below the
+ * best candidate score, so phenotypes stay exact.
+ *   gap_threshold: 1 .. 2^20 (HP_EINVAL otherwise); 1 with d_gap NULL is
+ *                  exactly hp_sequence_scan;
+ *   d_gap:         device int32[n] or NULL: E2 - E1, INT32_MAX when the box
+ *                  has a single conformation; clipped at gap_threshold when
+ *                  d_cand is given (pruned conformations are only known to
+ *                  lie that far above E1).
+ * Other arguments, ownership and errors as hp_sequence_scan. */
+int hp_sequence_scan_gap(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand, int32_t k,
+                         int32_t gap_threshold, int32_t* d_phen, int32_t* d_aux, int32_t* d_gap,
+                         uint64_t* d_counters, void* stream);
 
 /* ---- Learned proposal (no counterpart in the paper).  A network
  * N -> H1 -> H2 -> S (ReLU, softmax over the S classes) reads the bits of a

@@ -25,7 +25,7 @@ EXPORTS = (
     "hp_enumerate_structures", "hp_structs_info", "hp_structs_export", "hp_structs_free",
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
     "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
-    "hp_batch_plan_free", "hp_sequence_scan", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
+    "hp_batch_plan_free", "hp_sequence_scan", "hp_sequence_scan_gap", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
     "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_robustness_cross", "hp_stream_shards",
     "hp_neutral_components",
     "hp_last_error",
@@ -74,6 +74,7 @@ def lib():
         L.hp_batch_plan_launch.argtypes = [vp, vp]
         L.hp_batch_plan_status.argtypes = [vp, vp]
         L.hp_sequence_scan.argtypes = [vp, vp, ctypes.c_int64, vp, i32, vp, vp, vp, vp]
+        L.hp_sequence_scan_gap.argtypes = [vp, vp, ctypes.c_int64, vp, i32, i32, vp, vp, vp, vp, vp]
         L.hp_mlp_create.argtypes = [i32, i32, i32, i32, i32, vp, ctypes.POINTER(vp)]
         L.hp_mlp_free.argtypes = [vp]
         L.hp_mlp_free.restype = None
@@ -254,9 +255,11 @@ class BatchPlan:
             self._h = None
 
 
-def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, stream=None):
-    """Phenotypes of arbitrary ids (hp_sequence_scan); cand: int32 [n, k] candidate conformations or None.
-    Returns phen (and aux if requested); counters (int64[2] CUDA tensor) accumulates
+def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, stream=None, gap_threshold=1,
+                  gaps=False):
+    """Phenotypes of arbitrary ids (hp_sequence_scan, or hp_sequence_scan_gap for gap_threshold > 1 or
+    gaps); cand: int32 [n, k] candidate conformations or None.  Returns phen, then aux and the int32
+    energy gaps E2 - E1 in that order when requested; counters (int64[2] CUDA tensor) accumulates
     (conformations evaluated exactly, contact-count group bounds evaluated)."""
     import torch
 
@@ -265,6 +268,7 @@ def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, st
         raise TypeError("ids must be int64 (bit patterns of uint64 ids)")
     phen = torch.empty(n, dtype=torch.int32, device=ids.device)
     ax = torch.empty(n, dtype=torch.int32, device=ids.device) if aux else None
+    gp = torch.empty(n, dtype=torch.int32, device=ids.device) if gaps else None
     k = 0
     pc = None
     if cand is not None:
@@ -272,11 +276,18 @@ def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, st
             raise ValueError("cand must be [n, k]")
         k = cand.shape[1]
         pc = _dptr(cand, torch.int32, "cand")
-    _check(lib().hp_sequence_scan(structs.handle, ctypes.c_void_p(ids.data_ptr()), n, pc, k,
-                                  _dptr(phen, torch.int32, "phen"), _dptr(ax, torch.int32, "aux") if aux else None,
-                                  _dptr(counters, torch.int64, "counters") if counters is not None else None,
-                                  _stream_ptr(stream)))
-    return (phen, ax) if aux else phen
+    pids = ctypes.c_void_p(ids.data_ptr())
+    pphen = _dptr(phen, torch.int32, "phen")
+    pax = _dptr(ax, torch.int32, "aux") if aux else None
+    pcnt = _dptr(counters, torch.int64, "counters") if counters is not None else None
+    if gap_threshold == 1 and not gaps:
+        _check(lib().hp_sequence_scan(structs.handle, pids, n, pc, k, pphen, pax, pcnt, _stream_ptr(stream)))
+    else:
+        _check(lib().hp_sequence_scan_gap(structs.handle, pids, n, pc, k, int(gap_threshold), pphen, pax,
+                                          _dptr(gp, torch.int32, "gaps") if gaps else None, pcnt,
+                                          _stream_ptr(stream)))
+    out = (phen,) + ((ax,) if aux else ()) + ((gp,) if gaps else ())
+    return out if len(out) > 1 else phen
 
 
 class MLP:

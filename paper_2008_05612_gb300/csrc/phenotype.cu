@@ -795,12 +795,14 @@ extern "C" int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_
                                 int32_t* d_phen, int32_t* d_argmin_aux, void* stream) {
   if (!s) return hp::fail(HP_EINVAL, "hp_phenotype_map: library is NULL");
   if (!d_phen) return hp::fail(HP_EINVAL, "hp_phenotype_map: d_phen is NULL");
-  if (gap_threshold != 1) return hp::fail(HP_EUNSUPPORTED, "hp_phenotype_map: only gap_threshold 1 is implemented");
+  if (gap_threshold < 1) return hp::fail(HP_EINVAL, "hp_phenotype_map: gap_threshold must be at least 1");
   if (s->N > 2 * hp::kMaxHalf) return hp::fail(HP_EUNSUPPORTED, "hp_phenotype_map: N > 40");
   if (seq_count == 0) return HP_OK;
   const unsigned long long space = 1ull << s->N;
   if (seq_begin >= space || seq_count > space - seq_begin)
     return hp::fail(HP_EINVAL, "hp_phenotype_map: sequence range exceeds 2^N");
+  // a threshold above 1 needs the second-lowest energy, which the tiled kernel does not keep
+  if (gap_threshold > 1) return hp::scan_range(s, seq_begin, seq_count, gap_threshold, d_phen, d_argmin_aux, stream);
   int r = s->tile_reg_bits, t = s->tile_size;
   if (!r) hp::default_tile_cfg(&r, &t);
   return hp::run_phenotype(&s, &seq_begin, &seq_count, 1, &d_phen, d_argmin_aux ? &d_argmin_aux : nullptr, r, t,

@@ -26,6 +26,14 @@
 //
 // Reductions use warp primitives: running best / count / first index per lane,
 // then __reduce_max_sync, __reduce_add_sync and __reduce_min_sync.
+//
+// Energy-gap threshold T >= 1 (Section 2.1; the Appendix C kernel keeps the
+// lowest and second-lowest energy): a sequence folds iff E2 - E1 >= T, E2 the
+// second-lowest energy counted with multiplicity.  The kernel variant with
+// GAP set also keeps each lane's second-best score; pruning then skips only
+// groups with U(A) <= x_cand - T, whose every conformation lies at least T
+// below the best score, so the phenotype stays exact and the gap is exact
+// below T (it is reported clipped at T when pruning).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,13 +57,16 @@ struct ScanParams {
   const int32_t* midx;       // original index per member
   const uint32_t* orig_rec;  // original-order records (candidates)
   const int32_t* conf_class;
-  const unsigned long long* ids;
+  const unsigned long long* ids;  // n sequence ids, or NULL for the range begin + [0, n) (GAP variant)
+  unsigned long long begin;
   const int32_t* cand;       // n x k original conformation indices (-1: none) or NULL
   int32_t* phen;
   int32_t* aux;
+  int32_t* gap;              // n energy gaps E2 - E1 or NULL (GAP variant)
   unsigned long long* counters;  // [0] conformations evaluated exactly, [1] group bounds evaluated
   long long n;
   int k, rec_words, NE, C, S_dir, ngroups, gpad, spad, prune;
+  int T;                     // energy-gap threshold (1 unless GAP)
 };
 
 __device__ __forceinline__ uint32_t even_of(unsigned long long g) {
@@ -85,12 +96,13 @@ __device__ __forceinline__ int score_of(const uint32_t* r, int NE, uint32_t e, u
   return 10 * A + 3 * B;
 }
 
+template <bool GAP>
 __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const ScanParams p) {
   const int lane = threadIdx.x & 31;
   const long long warps_total = (long long)gridDim.x * kScanWarps;
   unsigned long long n_exact = 0, n_bound = 0;
   for (long long q = (long long)blockIdx.x * kScanWarps + (threadIdx.x >> 5); q < p.n; q += warps_total) {
-    const unsigned long long g = p.ids[q];
+    const unsigned long long g = (GAP && !p.ids) ? p.begin + (unsigned long long)q : p.ids[q];
     const uint32_t e = even_of(g), o = odd_of(g);
     // candidate score: best exact score over the candidate conformations
     int cand = -1;
@@ -106,16 +118,23 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
       }
       cand = __reduce_max_sync(0xFFFFFFFFu, best);
     }
+    // a group survives when its bound reaches cut (T = 1: the candidate score itself)
+    const int cut = GAP ? cand - p.T + 1 : cand;
     int best = -1, cnt = 0, first = INT_MAX;
+    int sec = -1;  // GAP: best score of this lane's conformations other than one at `best`
     auto take = [&](int x, int orig) {
       n_exact++;
       if (x > best) {
+        if (GAP) sec = best;
         best = x;
         cnt = 1;
         first = orig;
       } else if (x == best) {
         cnt++;
         first = min(first, orig);
+        if (GAP) sec = best;
+      } else if (GAP) {
+        sec = max(sec, x);
       }
     };
     if (cand < 0) {
@@ -170,7 +189,7 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
         A = (__popc(e & cw[0]) + __popc(o & cw[3])) + 2 * (__popc(e & cw[1]) + __popc(o & cw[4])) +
             4 * (__popc(e & cw[2]) + __popc(o & cw[5]));
         n_bound++;
-        if (upper(A, p.C) >= cand) n = cb1 - cb0;
+        if (upper(A, p.C) >= cut) n = cb1 - cb0;
       }
 #pragma unroll
       for (int k = 0; k < 6; k++) cw[k] = nw[k];
@@ -213,7 +232,19 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
     const int M = __reduce_max_sync(0xFFFFFFFFu, best);
     const int total = __reduce_add_sync(0xFFFFFFFFu, best == M ? cnt : 0);
     const int f = __reduce_min_sync(0xFFFFFFFFu, best == M ? first : INT_MAX);
-    if (lane == 0) {
+    if (GAP) {
+      // second-best score over the warp: the best itself when it is tied, else the larger of the
+      // lanes' second-best (lanes at M) and best (other lanes) scores; -1 when there is none
+      const int x2 = total >= 2 ? M : __reduce_max_sync(0xFFFFFFFFu, best == M ? sec : best);
+      int gap = x2 < 0 ? INT_MAX : M - x2;
+      if (p.prune) gap = min(gap, p.T);
+      if (lane == 0) {
+        const int cls = (f >= 0 && f < p.S_dir) ? __ldg(p.conf_class + f) : -1;
+        p.phen[q] = gap >= p.T ? cls : -1;
+        if (p.aux) p.aux[q] = cls;
+        if (p.gap) p.gap[q] = gap;
+      }
+    } else if (lane == 0) {
       const int cls = (f >= 0 && f < p.S_dir) ? __ldg(p.conf_class + f) : -1;
       p.phen[q] = (total == 1 || p.S_dir == 1) ? cls : -1;
       if (p.aux) p.aux[q] = cls;
@@ -313,12 +344,14 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
 
 }  // namespace hp
 
-extern "C" int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand,
-                                int32_t k, int32_t* d_phen, int32_t* d_aux, uint64_t* d_counters, void* stream) {
-  if (!s || !d_ids || !d_phen) return hp::fail(HP_EINVAL, "hp_sequence_scan: NULL argument");
-  if (n < 0 || k < 0 || (d_cand && k == 0)) return hp::fail(HP_EINVAL, "hp_sequence_scan: bad sizes");
-  if (s->N > 2 * hp::kMaxHalf) return hp::fail(HP_EUNSUPPORTED, "hp_sequence_scan: N > 40");
-  if (n == 0) return HP_OK;
+namespace {
+
+constexpr int kMaxGapThreshold = 1 << 20;
+
+// One launch of the scan over n ids (d_ids) or over the range begin + [0, n) (d_ids NULL, GAP only).
+int launch_scan(const hp_structs* s, const uint64_t* d_ids, uint64_t begin, int64_t n, const int32_t* d_cand,
+                int32_t k, int32_t T, bool gap_variant, int32_t* d_phen, int32_t* d_aux, int32_t* d_gap,
+                uint64_t* d_counters, cudaStream_t stream) {
   hp::DevTables* dt = nullptr;
   int rc = hp::scan_tables(s, &dt);
   if (rc != HP_OK) return rc;
@@ -331,9 +364,11 @@ extern "C" int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int6
   p.orig_rec = dt->rec;
   p.conf_class = dt->conf_class;
   p.ids = reinterpret_cast<const unsigned long long*>(d_ids);
+  p.begin = begin;
   p.cand = d_cand;
   p.phen = d_phen;
   p.aux = d_aux;
+  p.gap = d_gap;
   p.counters = reinterpret_cast<unsigned long long*>(d_counters);
   p.n = n;
   p.k = k;
@@ -345,13 +380,51 @@ extern "C" int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int6
   p.gpad = dt->scan_gpad;
   p.spad = dt->scan_spad;
   p.prune = d_cand != nullptr;
+  p.T = T;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long blocks = (n + kScanWarps - 1) / kScanWarps;
   blocks = std::min<long long>(blocks, (long long)sms * 8);
-  seq_scan_kernel<<<(unsigned)blocks, 32 * kScanWarps, 0, (cudaStream_t)stream>>>(p);
+  if (gap_variant)
+    seq_scan_kernel<true><<<(unsigned)blocks, 32 * kScanWarps, 0, stream>>>(p);
+  else
+    seq_scan_kernel<false><<<(unsigned)blocks, 32 * kScanWarps, 0, stream>>>(p);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return hp::cuda_fail(e, "hp_sequence_scan: launch");
+  if (e != cudaSuccess) return hp::cuda_fail(e, "per-sequence scan: launch");
   return HP_OK;
+}
+
+}  // namespace
+
+namespace hp {
+
+int scan_range(const hp_structs* s, uint64_t begin, uint64_t count, int32_t gap_threshold, int32_t* d_phen,
+               int32_t* d_aux, void* stream) {
+  if (gap_threshold < 1 || gap_threshold > kMaxGapThreshold)
+    return fail(HP_EINVAL, "gap_threshold must be in [1, 2^20]");
+  if (count == 0) return HP_OK;
+  return launch_scan(s, nullptr, begin, (int64_t)count, nullptr, 0, gap_threshold, true, d_phen, d_aux, nullptr,
+                     nullptr, (cudaStream_t)stream);
+}
+
+}  // namespace hp
+
+extern "C" int hp_sequence_scan_gap(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand,
+                                    int32_t k, int32_t gap_threshold, int32_t* d_phen, int32_t* d_aux,
+                                    int32_t* d_gap, uint64_t* d_counters, void* stream) {
+  if (!s || !d_ids || !d_phen) return hp::fail(HP_EINVAL, "hp_sequence_scan: NULL argument");
+  if (n < 0 || k < 0 || (d_cand && k == 0)) return hp::fail(HP_EINVAL, "hp_sequence_scan: bad sizes");
+  if (gap_threshold < 1 || gap_threshold > kMaxGapThreshold)
+    return hp::fail(HP_EINVAL, "hp_sequence_scan: gap_threshold must be in [1, 2^20]");
+  if (s->N > 2 * hp::kMaxHalf) return hp::fail(HP_EUNSUPPORTED, "hp_sequence_scan: N > 40");
+  if (n == 0) return HP_OK;
+  const bool gap_variant = gap_threshold != 1 || d_gap != nullptr;
+  return launch_scan(s, d_ids, 0, n, d_cand, k, gap_threshold, gap_variant, d_phen, d_aux, d_gap, d_counters,
+                     (cudaStream_t)stream);
+}
+
+extern "C" int hp_sequence_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand,
+                                int32_t k, int32_t* d_phen, int32_t* d_aux, uint64_t* d_counters, void* stream) {
+  return hp_sequence_scan_gap(s, d_ids, n, d_cand, k, 1, d_phen, d_aux, nullptr, d_counters, stream);
 }

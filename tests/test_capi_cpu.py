@@ -57,10 +57,17 @@ def test_bad_arguments_return_status():
     assert b"site" in L.hp_last_error()
     assert L.hp_structs_info(None, None, None, None, None) == hp.HP_EINVAL
     s = hp.Structs((2, 3))
-    # range beyond 2^N, unsupported threshold, NULL output: rejected before any CUDA call
+    # range beyond 2^N, threshold out of [1, 2^20], NULL output: rejected before any CUDA call
     assert L.hp_phenotype_map(s.handle, 60, 8, 1, ctypes.c_void_p(16), None, None) == hp.HP_EINVAL
-    assert L.hp_phenotype_map(s.handle, 0, 8, 2, ctypes.c_void_p(16), None, None) == hp.HP_EUNSUPPORTED
+    assert L.hp_phenotype_map(s.handle, 60, 8, 3, ctypes.c_void_p(16), None, None) == hp.HP_EINVAL
+    assert L.hp_phenotype_map(s.handle, 0, 8, 0, ctypes.c_void_p(16), None, None) == hp.HP_EINVAL
+    assert L.hp_phenotype_map(s.handle, 0, 8, (1 << 20) + 1, ctypes.c_void_p(16), None, None) == hp.HP_EINVAL
     assert L.hp_phenotype_map(s.handle, 0, 8, 1, None, None, None) == hp.HP_EINVAL
+    p16 = ctypes.c_void_p(16)
+    assert L.hp_sequence_scan_gap(s.handle, p16, 4, None, 0, 0, p16, None, None, None, None) == hp.HP_EINVAL
+    assert L.hp_sequence_scan_gap(s.handle, p16, 4, None, 0, (1 << 20) + 1, p16, None, None, None, None) == hp.HP_EINVAL
+    assert L.hp_sequence_scan_gap(s.handle, None, 4, None, 0, 2, p16, None, None, None, None) == hp.HP_EINVAL
+    assert L.hp_sequence_scan_gap(s.handle, p16, 4, p16, 0, 2, p16, None, None, None, None) == hp.HP_EINVAL
     assert L.hp_designability(None, 4, 3, None, None) == hp.HP_EINVAL
     assert L.hp_robustness(ctypes.c_void_p(16), 50, 3, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == hp.HP_EINVAL
     assert L.hp_neutral_components(ctypes.c_void_p(16), 36, 3, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == hp.HP_EUNSUPPORTED

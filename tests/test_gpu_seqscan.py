@@ -80,3 +80,62 @@ def test_pruned_scan_matches_exhaustive_block(hp):
     ids = np.arange(base, base + (1 << 16), dtype=np.uint64)[::7]
     phen = hp.sequence_scan(s, ids_tensor(ids))
     np.testing.assert_array_equal(phen.cpu().numpy(), block.cpu().numpy()[::7])
+
+
+@pytest.mark.parametrize("dims,n", [((3, 3), 512), ((4, 4), 1 << 16), ((3, 3, 3), 1200), ((6, 6), 400)])
+def test_gap_thresholds_and_gaps(hp, obox, dims, n):
+    """Energy-gap thresholds T > 1 (Section 2.1) and the gap E2 - E1 itself (Appendix C returns
+    E1 - E2): plain scan exact; pruned scan exact in the phenotype and in the gap clipped at T."""
+    s = hp.Structs(dims)
+    o = obox(dims)
+    ids = np.arange(n, dtype=np.uint64) if n == (1 << s.N) else inputs.sample_ids(s.N, n, seed=23)
+    t = ids_tensor(ids)
+    _, want_aux, want_gap = o.phenotypes(ids, aux=True, gaps=True)
+    rnd = conformations_of_classes(s, (inputs.sample_ids(20, n * 2, seed=9) % np.uint64(s.S)).astype(np.int64).reshape(n, 2), 4)
+    best = conformations_of_classes(s, want_aux[:, None], 2)
+    for T in (1, 2, 3, 10, 13, 23, 40):
+        want = np.where(want_gap >= T, want_aux, -1)  # the oracle's threshold rule, pinned on the CPU
+        phen, aux, gap = hp.sequence_scan(s, t, aux=True, gap_threshold=T, gaps=True)
+        np.testing.assert_array_equal(phen.cpu().numpy(), want)
+        np.testing.assert_array_equal(aux.cpu().numpy(), want_aux)
+        np.testing.assert_array_equal(gap.cpu().numpy(), want_gap)
+        for cand in (best, rnd):
+            cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+            p2, g2 = hp.sequence_scan(s, t, cand=torch.from_numpy(cand).cuda(), gap_threshold=T, gaps=True,
+                                      counters=cnt)
+            np.testing.assert_array_equal(p2.cpu().numpy(), want)
+            np.testing.assert_array_equal(g2.cpu().numpy(), np.minimum(want_gap, T))
+            assert int(cnt[0]) <= n * s.S_dir
+        # without the gap output the threshold-T phenotypes are the same
+        np.testing.assert_array_equal(hp.sequence_scan(s, t, gap_threshold=T).cpu().numpy(), want)
+
+
+def test_threshold_1_gap_variant_equals_plain_scan(hp):
+    s = hp.Structs((3, 3, 3))
+    t = ids_tensor(inputs.sample_ids(27, 3000, seed=41))
+    p1, a1 = hp.sequence_scan(s, t, aux=True)
+    p2, a2, g2 = hp.sequence_scan(s, t, aux=True, gaps=True)
+    assert torch.equal(p1, p2) and torch.equal(a1, a2)
+    assert torch.equal(p2 >= 0, g2 >= 1)
+
+
+def test_single_conformation_box_gap(hp):
+    s = hp.Structs((2, 2))
+    t = ids_tensor(np.arange(16, dtype=np.uint64))
+    phen, gap = hp.sequence_scan(s, t, gap_threshold=1000, gaps=True)
+    assert (phen == 0).all() and (gap == np.iinfo(np.int32).max).all()
+
+
+@pytest.mark.parametrize("dims,begin,count", [((4, 4), 0, 1 << 16), ((3, 3, 3), 3 << 20, 1500), ((4, 5), 12345, 777)])
+def test_map_at_threshold_above_1(hp, obox, dims, begin, count):
+    """hp_phenotype_map with gap_threshold > 1 (the per-sequence scan over the range), with aux."""
+    s = hp.Structs(dims)
+    o = obox(dims)
+    ids = np.arange(begin, begin + count, dtype=np.uint64)
+    _, want_aux, want_gap = o.phenotypes(ids, aux=True, gaps=True)
+    for T in (2, 10, 23):
+        want = np.where(want_gap >= T, want_aux, -1)
+        aux = torch.empty(count, dtype=torch.int32, device="cuda")
+        got = hp.phenotype_map(s, begin, count, aux=aux, gap_threshold=T)
+        np.testing.assert_array_equal(got.cpu().numpy(), want)
+        np.testing.assert_array_equal(aux.cpu().numpy(), want_aux)
