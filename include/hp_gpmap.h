@@ -225,7 +225,9 @@ int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t k, int32_t*
 int hp_mlp_status(hp_mlp* m, void* stream);
 
 /* Expand classes (device int32[n x k], -1 allowed) into their conformations:
- * d_cand[n x 2k], entry 2j + q = q-th conformation of class j or -1. */
+ * d_cand[n x 2k], entry 2j + q = q-th conformation of class j or -1.
+ * n >= 0 and k >= 1 (HP_EINVAL otherwise).  The class tables are built on the
+ * device on first use (synchronous upload); the expansion is stream-ordered. */
 int hp_proposal_conformations(const hp_structs* s, const int32_t* d_top, int64_t n, int32_t k, int32_t* d_cand,
                               void* stream);
 

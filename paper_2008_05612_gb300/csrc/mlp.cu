@@ -976,6 +976,7 @@ extern "C" int hp_mlp_logits(hp_mlp* m, const uint64_t* d_ids, int32_t n, float*
 extern "C" int hp_proposal_conformations(const hp_structs* s, const int32_t* d_top, int64_t n, int32_t k, int32_t* d_cand,
                                          void* stream) {
   if (!s || !d_top || !d_cand) return hp::fail(HP_EINVAL, "hp_proposal_conformations: NULL argument");
+  if (n < 0 || k < 1) return hp::fail(HP_EINVAL, "hp_proposal_conformations: n must be >= 0 and k >= 1");
   hp::DevTables* dt = nullptr;
   int rc = hp::device_tables(s, &dt);
   if (rc != HP_OK) return rc;
@@ -991,7 +992,14 @@ extern "C" int hp_proposal_conformations(const hp_structs* s, const int32_t* d_t
     if (e == cudaSuccess) e = cudaMalloc(&dt->class_nconf, (size_t)s->S * 4);
     if (e == cudaSuccess) e = cudaMemcpy(dt->class_first, first.data(), (size_t)s->S * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dt->class_nconf, cnt.data(), (size_t)s->S * 4, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return hp::cuda_fail(e, "hp_proposal_conformations: class tables");
+    if (e != cudaSuccess) {
+      // leave no half-built table behind: the next call rebuilds both
+      cudaFree(dt->class_first);
+      cudaFree(dt->class_nconf);
+      dt->class_first = nullptr;
+      dt->class_nconf = nullptr;
+      return hp::cuda_fail(e, "hp_proposal_conformations: class tables");
+    }
   }
   const long long total = n * (long long)k;
   if (total > 0)

@@ -68,6 +68,8 @@ def test_bad_arguments_return_status():
     assert L.hp_sequence_scan_gap(s.handle, p16, 4, None, 0, (1 << 20) + 1, p16, None, None, None, None) == hp.HP_EINVAL
     assert L.hp_sequence_scan_gap(s.handle, None, 4, None, 0, 2, p16, None, None, None, None) == hp.HP_EINVAL
     assert L.hp_sequence_scan_gap(s.handle, p16, 4, p16, 0, 2, p16, None, None, None, None) == hp.HP_EINVAL
+    assert L.hp_proposal_conformations(s.handle, p16, 4, 0, p16, None) == hp.HP_EINVAL
+    assert L.hp_proposal_conformations(s.handle, p16, -1, 2, p16, None) == hp.HP_EINVAL
     assert L.hp_designability(None, 4, 3, None, None) == hp.HP_EINVAL
     assert L.hp_robustness(ctypes.c_void_p(16), 50, 3, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == hp.HP_EINVAL
     assert L.hp_neutral_components(ctypes.c_void_p(16), 36, 3, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == hp.HP_EUNSUPPORTED
