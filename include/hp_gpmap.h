@@ -73,11 +73,10 @@ void hp_structs_free(hp_structs* s);
  * seq_count) (Section 2.1; Appendix C kernel semantics).
  *   gap_threshold: minimum energy gap E2 - E1 (x 10 units, E2 the second-
  *                  lowest energy counted with multiplicity) for a sequence to
- *                  fold; 1 = strict uniqueness (the paper's value) runs the
- *                  tiled map kernel; values in [2, 2^20] run the per-sequence
- *                  scan of hp_sequence_scan_gap over the range (exact, slower,
- *                  stream-ordered without synchronising); < 1 or > 2^20 give
- *                  HP_EINVAL.
+ *                  fold; 1 = strict uniqueness (the paper's value); values in
+ *                  [2, 2^20] run a variant of the map kernel that also keeps
+ *                  the second-best tile maximum, always in the default shape
+ *                  (reg_bits 5, tile 256); < 1 or > 2^20 give HP_EINVAL.
  *   d_phen:        device int32[seq_count]; d_phen[k] = phenotype of
  *                  seq_begin + k: class id, or -1.
  *   d_argmin_aux:  optional device int32[seq_count] (NULL to skip): class of

@@ -79,10 +79,6 @@ int device_tables(const hp_structs* s, DevTables** out);
 int scan_tables(const hp_structs* s, DevTables** out);
 // Same, plus the table of reversal-canonical odd patterns (odd N).
 int half_tables(const hp_structs* s, DevTables** out);
-// Phenotypes (and aux labels) of the id range [begin, begin + count) at an energy-gap threshold,
-// one warp per sequence (the per-sequence scan); stream-ordered (stream: a cudaStream_t).
-int scan_range(const hp_structs* s, uint64_t begin, uint64_t count, int32_t gap_threshold, int32_t* d_phen,
-               int32_t* d_aux, void* stream);
 // Records are padded on the device to a multiple of this many conformations.
 constexpr int kRecPad = 256;
 }  // namespace hp

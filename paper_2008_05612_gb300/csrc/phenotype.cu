@@ -247,7 +247,10 @@ __device__ __forceinline__ void prefetch_first_tiles(const hp::PhenInst& in, uin
   }
 }
 
-template <class K>
+// GAP: energy-gap threshold above 1 (p.gap2 = 2 T in the doubled score units): pass 1 also keeps,
+// per field, the largest tile maximum outside the first tile reaching the best (in the state area,
+// unused during pass 1), and pass 2 counts the best tile's conformations within T of the best.
+template <class K, bool GAP>
 __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_constant__ hp::PhenParams p) {
   constexpr int R = K::R, T = K::T, P = K::P, kThreads = K::THREADS, CSTRIDE = K::CSTRIDE;
   extern __shared__ __align__(128) uint32_t smem[];
@@ -307,6 +310,8 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     uint32_t tmax[P], m1[P], ts[P];
 #pragma unroll
     for (int v = 0; v < P; v++) tmax[v] = m1[v] = ts[v] = 0u;
+    if (GAP)
+      for (int v = 0; v < P; v++) st_best[v * kThreads + tid] = 0u;  // 0: no other tile yet
     prefetch_first_tiles<T>(in, rawbuf, bars, issued);
     // coefficient records of tile t + 1 are produced halfway through the consumption of tile t
     // (double buffered).  No CTA barrier: the producer warps arrive on full[b] when a buffer is
@@ -387,6 +392,11 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         const uint32_t mb = m1[v] & 0xFFFEFFFEu;
         const uint32_t gt = __vcmpgtu2(tmax[v], m1[v]);
         const uint32_t eq = __vcmpeq2(tmax[v], mb);
+        if (GAP) {
+          // the tile that is not (or no longer) the first best one joins the other tiles' maximum
+          uint32_t* m2 = st_best + v * kThreads + tid;
+          *m2 = vmax2(*m2, (gt & mb) | (~gt & tmax[v]));
+        }
         m1[v] = (gt & tmax[v]) | (~gt & (m1[v] | (eq & 0x00010001u)));
         ts[v] = (gt & tpk) | (~gt & ts[v]);
         tmax[v] = 0u;
@@ -403,8 +413,14 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
 #pragma unroll
     for (int v = 0; v < P; v++) {
       uint32_t mv = m1[v], tv = ts[v];
+      const uint32_t m2v = GAP ? st_best[v * kThreads + tid] : 0u;
 #pragma unroll
       for (int h = 0; h < 2; h++) {
+        if (GAP) {
+          // another tile within T of the best: the best is not unique (marked like a tie)
+          const uint32_t f2 = (m2v >> (16 * h)) & 0xFFFFu;
+          if (f2 != 0u && ((mv >> (16 * h)) & 0xFFFEu) < f2 + p.gap2) mv |= 1u << (16 * h);
+        }
         const uint32_t field = (mv >> (16 * h)) & 0xFFFFu;
         const uint32_t rw = (uint32_t)h | ((uint32_t)v << 1) | role_hi;
         const bool valid = nroles >= kRoles || (rw >> nroles) == 0u;
@@ -456,10 +472,14 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
 #pragma unroll
             for (int j = 0; j < R - 1; j++)
               if ((v >> j) & 1) x += cs[K::TP_OFF + j];
-            const bool match = ((x >> (16 * h)) & 0xFFFFu) == want;  // padding scores 0 never match
+            const uint32_t xf = (x >> (16 * h)) & 0xFFFFu;
+            const bool match = xf == want;  // padding scores 0 never match
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, match);
             if (first < 0 && bal) first = t * T + i + __ffs(bal) - 1;
-            count += __popc(bal);
+            if (GAP)  // real conformations (padding is 0) within T of the best, the best included
+              count += __popc(__ballot_sync(0xFFFFFFFFu, xf >= 2u && xf + p.gap2 > want));
+            else
+              count += __popc(bal);
           }
           if (lane == src) {
             cmask &= ~(1ull << sf);
@@ -593,10 +613,10 @@ size_t smem_bytes(int max_rec_words) {
   return words * 4 + 6 * sizeof(uint64_t);
 }
 
-template <class K>
+template <class K, bool GAP = false>
 int launch_shape(const hp::PhenParams& prm, cudaStream_t stream, unsigned grid_limit) {
   const size_t smem = smem_bytes<K>(prm.max_rec_words);
-  auto kern = phenotype_kernel<K>;
+  auto kern = phenotype_kernel<K, GAP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return hp::cuda_fail(e, "cudaFuncSetAttribute(phenotype_kernel)");
   int dev = 0, sms = 0, per_sm = 0;
@@ -633,6 +653,8 @@ void default_tile_cfg(int* reg_bits, int* tile) {
 }
 
 int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit) {
+  // thresholds above 1 have one compiled shape (the default)
+  if (prm.gap2 > 2u) return launch_shape<Cfg<5, 256>, true>(prm, stream, grid_limit);
   switch (reg_bits * 1000 + tile) {
     case 4064: return launch_shape<Cfg<4, 64>>(prm, stream, grid_limit);
     case 4128: return launch_shape<Cfg<4, 128>>(prm, stream, grid_limit);
@@ -694,6 +716,7 @@ int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const 
   prm.ninst = n;
   prm.max_rec_words = 0;
   prm.one = 1u;
+  prm.gap2 = 2u;
   unsigned long long items = 0;
   int nb = 0;
   for (int q = 0; q < n; q++) {
@@ -759,11 +782,17 @@ int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const 
 
 int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
                   int32_t* const* d_phen, int32_t* const* d_aux, int reg_bits, int tile, cudaStream_t st,
-                  unsigned grid_limit) {
+                  unsigned grid_limit, int gap_threshold) {
   if (!tile_cfg_supported(reg_bits, tile)) return fail(HP_EINVAL, "unsupported tile configuration");
+  if (gap_threshold < 1 || gap_threshold > (1 << 20)) return fail(HP_EINVAL, "gap_threshold must be in [1, 2^20]");
+  if (gap_threshold > 1) {
+    reg_bits = 5;  // the shape compiled for thresholds above 1
+    tile = 256;
+  }
   PhenParams* prm = new (std::nothrow) PhenParams();
   if (!prm) return fail(HP_ENOMEM, "out of host memory");
   int rc = plan_phenotype(libs, begins, counts, n, d_phen, d_aux, tile, *prm);
+  prm->gap2 = 2u * (uint32_t)gap_threshold;
   if (rc != HP_OK || prm->total_items == 0) {
     delete prm;
     return rc;
@@ -795,16 +824,15 @@ extern "C" int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_
                                 int32_t* d_phen, int32_t* d_argmin_aux, void* stream) {
   if (!s) return hp::fail(HP_EINVAL, "hp_phenotype_map: library is NULL");
   if (!d_phen) return hp::fail(HP_EINVAL, "hp_phenotype_map: d_phen is NULL");
-  if (gap_threshold < 1) return hp::fail(HP_EINVAL, "hp_phenotype_map: gap_threshold must be at least 1");
+  if (gap_threshold < 1 || gap_threshold > (1 << 20))
+    return hp::fail(HP_EINVAL, "hp_phenotype_map: gap_threshold must be in [1, 2^20]");
   if (s->N > 2 * hp::kMaxHalf) return hp::fail(HP_EUNSUPPORTED, "hp_phenotype_map: N > 40");
   if (seq_count == 0) return HP_OK;
   const unsigned long long space = 1ull << s->N;
   if (seq_begin >= space || seq_count > space - seq_begin)
     return hp::fail(HP_EINVAL, "hp_phenotype_map: sequence range exceeds 2^N");
-  // a threshold above 1 needs the second-lowest energy, which the tiled kernel does not keep
-  if (gap_threshold > 1) return hp::scan_range(s, seq_begin, seq_count, gap_threshold, d_phen, d_argmin_aux, stream);
   int r = s->tile_reg_bits, t = s->tile_size;
   if (!r) hp::default_tile_cfg(&r, &t);
   return hp::run_phenotype(&s, &seq_begin, &seq_count, 1, &d_phen, d_argmin_aux ? &d_argmin_aux : nullptr, r, t,
-                           (cudaStream_t)stream, 0);
+                           (cudaStream_t)stream, 0, gap_threshold);
 }

@@ -43,6 +43,7 @@ struct PhenParams {
   unsigned long long total_items;
   PhenInst inst[kPhenMaxInst];
   PhenBlock blocks[kPhenMaxBlocks];
+  uint32_t gap2;       // 2 x the energy-gap threshold (2: strict uniqueness, the paper's threshold 1)
 };
 
 bool tile_cfg_supported(int reg_bits, int tile);
@@ -50,9 +51,10 @@ void default_tile_cfg(int* reg_bits, int* tile);
 int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
                    int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm);
 int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit);
-// plan + per-call control words + launch + error read-back (synchronises the stream)
+// plan + per-call control words + launch + error read-back (synchronises the stream); a
+// gap_threshold above 1 runs the one shape compiled for it (reg_bits 5, tile 256)
 int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
                   int32_t* const* d_phen, int32_t* const* d_aux, int reg_bits, int tile, cudaStream_t st,
-                  unsigned grid_limit);
+                  unsigned grid_limit, int gap_threshold = 1);
 
 }  // namespace hp

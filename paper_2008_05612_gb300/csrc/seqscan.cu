@@ -57,8 +57,7 @@ struct ScanParams {
   const int32_t* midx;       // original index per member
   const uint32_t* orig_rec;  // original-order records (candidates)
   const int32_t* conf_class;
-  const unsigned long long* ids;  // n sequence ids, or NULL for the range begin + [0, n) (GAP variant)
-  unsigned long long begin;
+  const unsigned long long* ids;  // n sequence ids
   const int32_t* cand;       // n x k original conformation indices (-1: none) or NULL
   int32_t* phen;
   int32_t* aux;
@@ -102,7 +101,7 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
   const long long warps_total = (long long)gridDim.x * kScanWarps;
   unsigned long long n_exact = 0, n_bound = 0;
   for (long long q = (long long)blockIdx.x * kScanWarps + (threadIdx.x >> 5); q < p.n; q += warps_total) {
-    const unsigned long long g = (GAP && !p.ids) ? p.begin + (unsigned long long)q : p.ids[q];
+    const unsigned long long g = p.ids[q];
     const uint32_t e = even_of(g), o = odd_of(g);
     // candidate score: best exact score over the candidate conformations
     int cand = -1;
@@ -348,8 +347,8 @@ namespace {
 
 constexpr int kMaxGapThreshold = 1 << 20;
 
-// One launch of the scan over n ids (d_ids) or over the range begin + [0, n) (d_ids NULL, GAP only).
-int launch_scan(const hp_structs* s, const uint64_t* d_ids, uint64_t begin, int64_t n, const int32_t* d_cand,
+// One launch of the scan over n ids.
+int launch_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand,
                 int32_t k, int32_t T, bool gap_variant, int32_t* d_phen, int32_t* d_aux, int32_t* d_gap,
                 uint64_t* d_counters, cudaStream_t stream) {
   hp::DevTables* dt = nullptr;
@@ -364,7 +363,6 @@ int launch_scan(const hp_structs* s, const uint64_t* d_ids, uint64_t begin, int6
   p.orig_rec = dt->rec;
   p.conf_class = dt->conf_class;
   p.ids = reinterpret_cast<const unsigned long long*>(d_ids);
-  p.begin = begin;
   p.cand = d_cand;
   p.phen = d_phen;
   p.aux = d_aux;
@@ -397,19 +395,6 @@ int launch_scan(const hp_structs* s, const uint64_t* d_ids, uint64_t begin, int6
 
 }  // namespace
 
-namespace hp {
-
-int scan_range(const hp_structs* s, uint64_t begin, uint64_t count, int32_t gap_threshold, int32_t* d_phen,
-               int32_t* d_aux, void* stream) {
-  if (gap_threshold < 1 || gap_threshold > kMaxGapThreshold)
-    return fail(HP_EINVAL, "gap_threshold must be in [1, 2^20]");
-  if (count == 0) return HP_OK;
-  return launch_scan(s, nullptr, begin, (int64_t)count, nullptr, 0, gap_threshold, true, d_phen, d_aux, nullptr,
-                     nullptr, (cudaStream_t)stream);
-}
-
-}  // namespace hp
-
 extern "C" int hp_sequence_scan_gap(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int32_t* d_cand,
                                     int32_t k, int32_t gap_threshold, int32_t* d_phen, int32_t* d_aux,
                                     int32_t* d_gap, uint64_t* d_counters, void* stream) {
@@ -420,7 +405,7 @@ extern "C" int hp_sequence_scan_gap(const hp_structs* s, const uint64_t* d_ids, 
   if (s->N > 2 * hp::kMaxHalf) return hp::fail(HP_EUNSUPPORTED, "hp_sequence_scan: N > 40");
   if (n == 0) return HP_OK;
   const bool gap_variant = gap_threshold != 1 || d_gap != nullptr;
-  return launch_scan(s, d_ids, 0, n, d_cand, k, gap_threshold, gap_variant, d_phen, d_aux, d_gap, d_counters,
+  return launch_scan(s, d_ids, n, d_cand, k, gap_threshold, gap_variant, d_phen, d_aux, d_gap, d_counters,
                      (cudaStream_t)stream);
 }
 

@@ -128,7 +128,8 @@ def test_single_conformation_box_gap(hp):
 
 @pytest.mark.parametrize("dims,begin,count", [((4, 4), 0, 1 << 16), ((3, 3, 3), 3 << 20, 1500), ((4, 5), 12345, 777)])
 def test_map_at_threshold_above_1(hp, obox, dims, begin, count):
-    """hp_phenotype_map with gap_threshold > 1 (the per-sequence scan over the range), with aux."""
+    """hp_phenotype_map with gap_threshold > 1 (the tiled kernel's gap variant) against the oracle:
+    one tile (4x4), several tiles and ragged aligned blocks (3x3x3, 4x5), with aux."""
     s = hp.Structs(dims)
     o = obox(dims)
     ids = np.arange(begin, begin + count, dtype=np.uint64)
@@ -139,3 +140,33 @@ def test_map_at_threshold_above_1(hp, obox, dims, begin, count):
         got = hp.phenotype_map(s, begin, count, aux=aux, gap_threshold=T)
         np.testing.assert_array_equal(got.cpu().numpy(), want)
         np.testing.assert_array_equal(aux.cpu().numpy(), want_aux)
+
+
+@pytest.mark.parametrize("dims,begin,count,sample", [((3, 3, 3), 5 << 22, 1 << 20, 1), ((6, 6), 7 << 30, 1 << 22, 64),
+                                                     ((2, 3, 4), 0, 1 << 24, 256)])
+def test_tiled_map_thresholds_match_the_scan(hp, dims, begin, count, sample):
+    """The tiled map at T > 1 against the per-sequence scan at T (checked against the oracle above)
+    on many tiles of conformations: 3x3x3 (404 tiles), 6x6 (224), 2x3x4 (even N, whole space)."""
+    s = hp.Structs(dims)
+    ids = torch.arange(begin, begin + count, sample, dtype=torch.int64, device="cuda")
+    m1 = hp.phenotype_map(s, begin, count)
+    for T in (2, 5, 13):
+        aux = torch.empty(count, dtype=torch.int32, device="cuda")
+        mT = hp.phenotype_map(s, begin, count, aux=aux, gap_threshold=T)
+        want, want_aux = hp.sequence_scan(s, ids, aux=True, gap_threshold=T)
+        assert torch.equal(mT[::sample], want) and torch.equal(aux[::sample], want_aux)
+        assert bool(((mT == -1) | (mT == m1)).all())  # raising T only turns folders into non-folders
+        m1 = mT
+
+
+def test_full_3x3x3_map_at_threshold_3(hp):
+    """Whole 3x3x3 space at T = 3: the reversal half enumeration and its mirrored writes."""
+    s = hp.Structs((3, 3, 3))
+    m = hp.phenotype_map(s, gap_threshold=3)
+    ids = torch.from_numpy(inputs.sample_ids(27, 1 << 15, seed=77).view(np.int64)).cuda()
+    assert torch.equal(m[ids], hp.sequence_scan(s, ids, gap_threshold=3))
+    g = ids
+    r = torch.zeros_like(g)
+    for i in range(27):
+        r |= ((g >> i) & 1) << (26 - i)
+    assert torch.equal(m[ids], m[r])
