@@ -564,7 +564,7 @@ def main():
                         "is the sequence range (no per-step input data)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "ALU lane-ops/s",
                      "frac": achieved / peak_ops, "traffic": TRAFFIC_PER_LAUNCH,
-                     "kernel": f"phenotype_kernel<Cfg<{tile_cfg[0]},{tile_cfg[1]}>>",
+                     "kernel": f"phenotype_kernel<Cfg<{tile_cfg[0]},{tile_cfg[1]}>, false>",
                      "peak_source": "derived: 64 ALU lane-ops/clk/SM x 152 SMs x max SM clock (no integer peak is measured "
                                     "by the driver)",
                      "note": "algorithmic ALU work = 0.5 packed max per performed sequence x conformation evaluation "
