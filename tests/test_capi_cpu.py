@@ -92,3 +92,16 @@ def test_stream_shards_rejects_a_small_window_before_device_work():
     assert e.value.code == hp.HP_EINVAL and "window" in str(e.value)
     with pytest.raises(hp.HPError):
         hp.stream_shards(s, 16)
+
+
+def test_no_cpu_fallback():
+    """Host tensors are refused and a map without a GPU raises: there is no CPU path."""
+    torch = pytest.importorskip("torch")
+    s = hp.Structs((2, 3))
+    with pytest.raises(TypeError):
+        hp.sequence_scan(s, torch.zeros(4, dtype=torch.int64))
+    with pytest.raises(TypeError):
+        hp.designability(torch.zeros(4, dtype=torch.int32), s.S)
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError):
+            hp.phenotype_map(s)
