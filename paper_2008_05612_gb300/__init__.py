@@ -276,7 +276,7 @@ def sequence_scan(structs: Structs, ids, cand=None, aux=False, counters=None, st
             raise ValueError("cand must be [n, k]")
         k = cand.shape[1]
         pc = _dptr(cand, torch.int32, "cand")
-    pids = ctypes.c_void_p(ids.data_ptr())
+    pids = _dptr(ids, torch.int64, "ids")
     pphen = _dptr(phen, torch.int32, "phen")
     pax = _dptr(ax, torch.int32, "aux") if aux else None
     pcnt = _dptr(counters, torch.int64, "counters") if counters is not None else None
@@ -320,7 +320,7 @@ class MLP:
         grads = [np.zeros(sh, dtype=np.float32) for sh in self._shapes]
         ptrs = (ctypes.c_void_p * 6)(*[g.ctypes.data for g in grads])
         loss = ctypes.c_float()
-        _check(lib().hp_mlp_gradients(self._h, ctypes.c_void_p(ids.data_ptr()), _dptr(labels, torch.int32, "labels"),
+        _check(lib().hp_mlp_gradients(self._h, _dptr(ids, torch.int64, "ids"), _dptr(labels, torch.int32, "labels"),
                                       ids.numel(), ptrs, ctypes.byref(loss), _stream_ptr(stream)))
         return loss.value, grads
 
@@ -328,7 +328,7 @@ class MLP:
         import torch
 
         loss = ctypes.c_float()
-        _check(lib().hp_mlp_train_step(self._h, ctypes.c_void_p(ids.data_ptr()), _dptr(labels, torch.int32, "labels"),
+        _check(lib().hp_mlp_train_step(self._h, _dptr(ids, torch.int64, "ids"), _dptr(labels, torch.int32, "labels"),
                                        ids.numel(), ctypes.c_float(lr), ctypes.byref(loss) if want_loss else None,
                                        _stream_ptr(stream)))
         return loss.value if want_loss else None
@@ -337,7 +337,7 @@ class MLP:
         import torch
 
         out = torch.empty((ids.numel(), self.S), dtype=torch.float32, device=ids.device)
-        _check(lib().hp_mlp_logits(self._h, ctypes.c_void_p(ids.data_ptr()), ids.numel(), _dptr(out, torch.float32, "out"),
+        _check(lib().hp_mlp_logits(self._h, _dptr(ids, torch.int64, "ids"), ids.numel(), _dptr(out, torch.float32, "out"),
                                    _stream_ptr(stream)))
         return out
 
@@ -345,7 +345,7 @@ class MLP:
         import torch
 
         out = torch.empty((ids.numel(), k), dtype=torch.int32, device=ids.device)
-        _check(lib().hp_mlp_topk(self._h, ctypes.c_void_p(ids.data_ptr()), ids.numel(), k, _dptr(out, torch.int32, "out"),
+        _check(lib().hp_mlp_topk(self._h, _dptr(ids, torch.int64, "ids"), ids.numel(), k, _dptr(out, torch.int32, "out"),
                                  _stream_ptr(stream)))
         return out
 

@@ -177,3 +177,14 @@ def test_trained_proposal_prunes_more_than_untrained(hp, trained_3x3x3):
         evals[name] = int(cnt[0])
     print("exact evaluations:", evals, "plain:", 2048 * s.S_dir)
     assert evals["trained"] < evals["untrained"] < 2048 * s.S_dir
+
+
+def test_host_or_strided_ids_are_refused(hp):
+    """ids must be contiguous int64 device tensors: the binding checks them before any launch."""
+    net = hp.MLP(27, 64, 96, 300, 512, init(27, 64, 96, 300, 11))
+    with pytest.raises(TypeError):
+        net.topk(torch.zeros(4, dtype=torch.int64), 1)
+    with pytest.raises(TypeError):
+        net.logits(torch.zeros(8, dtype=torch.int64, device="cuda")[::2])
+    with pytest.raises(TypeError):
+        net.train_step(torch.zeros(4, dtype=torch.int64), torch.zeros(4, dtype=torch.int32, device="cuda"), 1e-3)
