@@ -16,7 +16,12 @@
  *     chain reversal.  Every conformation competes; a sequence folds to the
  *     class of the unique lowest-energy conformation and otherwise gets the
  *     deleterious phenotype -1 (Section 2.1, energy-threshold paragraph, with
- *     threshold 1 in integer units as in Appendix C).
+ *     threshold 1 in integer units as in Appendix C).  Where a call takes a
+ *     gap_threshold T, a sequence folds iff E2 - E1 >= T, E2 the second-lowest
+ *     energy counted with multiplicity; T = 1 is the rule just stated.
+ *   - Box sizes: the enumeration time and the library grow quickly with N
+ *     (3x3x3: 103,346 conformations in about 0.5 s; 2x4x4: 4.4 million in
+ *     about 20 s); the map kernels take boxes with fewer than 65,535 classes.
  *   - Class ids are ranks of class representatives: the representative is
  *     the lexicographically smallest tuple (site(r_0), ..., site(r_{N-1})),
  *     site = x + Lx*(y + Ly*z), over G and both directions.
