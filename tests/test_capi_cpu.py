@@ -105,3 +105,18 @@ def test_no_cpu_fallback():
     if not torch.cuda.is_available():
         with pytest.raises(RuntimeError):
             hp.phenotype_map(s)
+
+
+def test_histogram_outputs_are_checked_before_any_launch():
+    """An output shorter than S + 1 counts, or on another device than the map, is refused by the
+    binding before the entry point could write past its end."""
+    torch = pytest.importorskip("torch")
+    phen = torch.zeros(16, dtype=torch.int32)
+    short = torch.zeros(10, dtype=torch.int64)
+    for fn in (hp.designability, hp.designability_noalloc):
+        with pytest.raises(hp.HPError) as e:
+            fn(phen, 10, short)
+        assert e.value.code == hp.HP_EINVAL and "S + 1" in str(e.value)
+        with pytest.raises(hp.HPError) as e:
+            fn(phen, 0, short)
+        assert e.value.code == hp.HP_EINVAL

@@ -131,3 +131,29 @@ def test_golden_file_is_well_formed():
         pins = json.load(f)
     assert pins["folds_3x3x3"]["value"] - pins["undesignable_3x3x3"]["value"] == pins["designable_3x3x3"]["value"]
     assert abs(pins["fold_fraction_3x3x3"]["value"] + pins["deleterious_fraction_3x3x3"]["value"] - 1) < 1e-9
+
+
+def brute_neighbourhood(phen, N, S, q):
+    """Eq. 2 numerators of row q by direct counting: for every genotype of phenotype q and every
+    single flip, one count at the neighbour's phenotype (index S for -1)."""
+    row = np.zeros(S + 1, dtype=np.uint64)
+    g = np.nonzero(phen == q)[0]
+    for i in range(N):
+        p = phen[g ^ (1 << i)]
+        np.add.at(row, np.where(p < 0, S, p), 1)
+    return row
+
+
+@pytest.mark.parametrize("N,S,seed", [(10, 4, 2), (12, 9, 3)])
+def test_neighbourhood_every_row_matches_brute_force(N, S, seed):
+    """Every entry of every row (q = -1 .. S-1), on maps whose rows have many nonzero entries."""
+    phen = synthetic_map(N, S, seed)
+    for q in range(-1, S):
+        np.testing.assert_array_equal(oracle.neighbourhood(phen, N, S, q), brute_neighbourhood(phen, N, S, q))
+
+
+def test_neighbourhood_every_row_of_the_4x4_map(obox):
+    b = obox((4, 4))
+    phen = b.full_map()
+    for q in range(-1, b.S):
+        np.testing.assert_array_equal(oracle.neighbourhood(phen, b.N, b.S, q), brute_neighbourhood(phen, b.N, b.S, q))
