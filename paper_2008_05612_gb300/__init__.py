@@ -28,7 +28,7 @@ EXPORTS = (
     "hp_batch_plan_free", "hp_sequence_scan", "hp_sequence_scan_gap", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
     "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_robustness_cross", "hp_stream_shards",
     "hp_neutral_components",
-    "hp_last_error",
+    "hp_last_error", "hp_set_wait_limit",
 )
 _VOID = ("hp_structs_free", "hp_last_error", "hp_batch_plan_free", "hp_mlp_free")
 
@@ -94,11 +94,17 @@ def lib():
         L.hp_robustness_cross.argtypes = [vp, vp, u64, i32, vp, vp, vp]
         L.hp_stream_shards.argtypes = [vp, i32, i32, ctypes.c_char_p, vp, vp, vp, vp, vp]
         L.hp_last_error.restype = ctypes.c_char_p
+        L.hp_set_wait_limit.argtypes = [ctypes.c_int64]
         for name in EXPORTS:
             if name not in _VOID:
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
+
+
+def set_wait_limit(polls: int):
+    """hp_set_wait_limit: poll limit of the kernels' bounded waits for later launches (< 0: built-in)."""
+    _check(lib().hp_set_wait_limit(int(polls)))
 
 
 def _check(rc: int):
@@ -365,13 +371,27 @@ def proposal_conformations(structs: Structs, top, stream=None):
     return cand
 
 
+def _hist_out_checks(phen, S: int, out, name: str):
+    """Refuse, before any launch, an output too short for S + 1 counts or tensors on different devices:
+    the entry point writes S + 1 uint64 counts and launches on the current device."""
+    if S < 1:
+        raise HPError(HP_EINVAL, f"{name}: S must be >= 1")
+    if out.numel() < S + 1:
+        raise HPError(HP_EINVAL, f"{name}: out holds {out.numel()} counts, S + 1 = {S + 1} are written")
+    if out.device != phen.device:
+        raise HPError(HP_EINVAL, f"{name}: phen ({phen.device}) and out ({out.device}) are on different devices")
+
+
 def designability(phen, S: int, out=None, stream=None):
+    """Designability N_p (hp_designability): int64[S + 1], index S counts -1."""
     import torch
 
     if out is None:
         out = torch.empty(S + 1, dtype=torch.int64, device=phen.device)
-    _check(lib().hp_designability(_dptr(phen, torch.int32, "phen"), phen.numel(), S, _dptr(out, torch.int64, "out"),
-                                  _stream_ptr(stream)))
+    _hist_out_checks(phen, S, out, "designability")
+    pp, po = _dptr(phen, torch.int32, "phen"), _dptr(out, torch.int64, "out")
+    with torch.cuda.device(phen.device):
+        _check(lib().hp_designability(pp, phen.numel(), S, po, _stream_ptr(stream)))
     return out
 
 
@@ -380,8 +400,10 @@ def designability_noalloc(phen, S: int, out, stream=None):
     allocation by the library (scratch is a static device array shared by all calls)."""
     import torch
 
-    _check(lib().hp_designability_noalloc(_dptr(phen, torch.int32, "phen"), phen.numel(), S,
-                                          _dptr(out, torch.int64, "out"), _stream_ptr(stream)))
+    _hist_out_checks(phen, S, out, "designability_noalloc")
+    pp, po = _dptr(phen, torch.int32, "phen"), _dptr(out, torch.int64, "out")
+    with torch.cuda.device(phen.device):
+        _check(lib().hp_designability_noalloc(pp, phen.numel(), S, po, _stream_ptr(stream)))
     return out
 
 
