@@ -274,39 +274,55 @@ def run_map_only(args):
     return 0
 
 
+def map_block_6x6(hp, torch, peak_ops: float, bits: int = 27, reps: int = 3):
+    """The metric's second box: the 6x6 phenotype map of the aligned id block [0, 2^bits) (every id of the
+    block is evaluated: 6x6 is an even chain, so there is no reversal half enumeration), 1 warm-up + `reps`
+    launches timed with CUDA events on the launching stream."""
+    s = hp.Structs((6, 6))
+    n = 1 << bits
+    phen = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    hp.phenotype_map(s, 0, n, out=phen)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        hp.phenotype_map(s, 0, n, out=phen)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    evals = n * s.S_dir
+    achieved = 0.5 * evals / (ms * 1e-3)
+    folded = int((phen >= 0).sum().item())
+    return {"workload": f"6x6 phenotype map of ids [0, 2^{bits}) x {s.S_dir} conformations ({s.S} classes)",
+            "map_ms": ms, "evals_per_s": evals / (ms * 1e-3), "sequences_per_s": n / (ms * 1e-3),
+            "fold_fraction": folded / n,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "ALU lane-ops/s",
+                         "frac": achieved / peak_ops, "kernel": "phenotype_kernel<Cfg<5,256>, false>",
+                         "note": "0.5 packed max per performed evaluation (all 2^27 ids of the block are evaluated)"}}
+
+
 PROPOSAL_ROWS = 16384  # ids per proposal chunk (the network's max_batch)
 
 
-def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 1 << 16, k: int = 4,
-                batch: int = 4096, lr: float = 1e-3):
-    """Learned proposal + bound-pruned scan vs the plain per-sequence scan on the same seeded ids.
-
-    Labels: the lowest-index minimiser (aux output) of the exhaustive kernel's full map; training ids:
-    the seeded 1-in-10 sample of the whole space; network N -> 512 -> 512 -> S trained on the GPU with
-    the library's kernels.  Evaluation: `eval_n` seeded ids, timed with CUDA events: plain full scan vs
-    (network top-k + candidate expansion + pruned scan); phenotypes must agree exactly."""
+def proposal_params(N, S):
     from paper_2008_05612_gb300 import inputs
 
+    return [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
+            inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
+            inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
+
+
+def train_proposal(hp, s, torch, tids, tlab, epochs: float = 1.0, batch: int = 4096, lr: float = 1e-3):
+    """N -> 512 -> 512 -> S network trained on the GPU with the library's kernels (one Adam step per batch
+    of `batch` (id, label) pairs, `epochs` passes over the training set); returns (trained, untrained, info)."""
     N, S = s.N, s.S
-    dev = "cuda"
-    phen = torch.empty(1 << N, dtype=torch.int32, device=dev)
-    aux = torch.empty(1 << N, dtype=torch.int32, device=dev)
-    hp.phenotype_map(s, 0, 1 << N, out=phen, aux=aux)
-    ids_all = np.arange(1 << N, dtype=np.uint64)
-    train_ids = ids_all[inputs.training_mask(ids_all)]
-    del ids_all
-    tids = torch.from_numpy(train_ids.view(np.int64)).to(dev)
-    tlab = aux[tids]
-    del phen, aux
-    params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
-              inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
-              inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
-    # rows per forward chunk: training steps use `batch` of them, the proposal runs 16384 at a time
+    params = proposal_params(N, S)
     net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
     untrained = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
-    steps = max(1, int(train_fraction_epochs * tids.numel() / batch))
-    gen = torch.Generator(device=dev).manual_seed(0)
-    perm = torch.randperm(tids.numel(), device=dev, generator=gen)
+    steps = max(1, int(epochs * tids.numel() / batch))
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    perm = torch.randperm(tids.numel(), device="cuda", generator=gen)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     first_loss = last_loss = None
@@ -319,10 +335,17 @@ def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 
         if st == steps - 1:
             last_loss = loss
     torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    net.status()
+    info = {"train_ids": int(tids.numel()), "train_steps": steps, "batch": batch, "lr": lr,
+            "train_s": time.perf_counter() - t0, "loss_first": first_loss, "loss_last": last_loss}
+    return net, untrained, info
 
-    ev = torch.from_numpy(inputs.sample_ids(N, eval_n, seed=123).view(np.int64)).to(dev)
+
+def compare_on_ids(hp, s, torch, ev, models, k: int = 4):
+    """Plain per-sequence scan vs (network top-k + candidate expansion + pruned scan) on the same ids,
+    CUDA-event timed (1 warm-up + 3 calls); phenotypes must agree exactly."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = ev.numel()
 
     def timed(fn, reps=3):
         fn()
@@ -335,9 +358,9 @@ def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 
         return out, e0.elapsed_time(e1) / reps
 
     plain, ms_plain = timed(lambda: hp.sequence_scan(s, ev))
-    res = {}
-    for name, model in (("trained", net), ("untrained", untrained)):
-        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+    res = {"plain_per_sequence": {"ms": ms_plain, "sequences_per_s": n / (ms_plain * 1e-3)}}
+    for name, model in models.items():
+        cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
 
         def learned():
             cand = hp.proposal_conformations(s, model.topk(ev, k))
@@ -348,16 +371,101 @@ def learned_leg(hp, s, torch, train_fraction_epochs: float = 1.0, eval_n: int = 
         model.status()
         exact = int(cnt[0]) / 4  # four calls accumulated (warm-up + 3 timed)
         bounds = int(cnt[1]) / 4
-        res[name] = {"ms": ms, "ms_proposal": ms_prop, "sequences_per_s": eval_n / (ms * 1e-3),
-                     "exact_eval_fraction": exact / (eval_n * s.S_dir),
-                     "group_bounds_per_sequence": bounds / eval_n,
+        res[name] = {"ms": ms, "ms_proposal": ms_prop, "sequences_per_s": n / (ms * 1e-3),
+                     "exact_eval_fraction": exact / (n * s.S_dir), "group_bounds_per_sequence": bounds / n,
                      "mismatches_vs_plain": int((out != plain).sum().item())}
-    return {
-        "box": "3x3x3", "train_ids": int(tids.numel()), "train_steps": steps, "batch": batch, "lr": lr,
-        "train_s": train_s, "loss_first": first_loss, "loss_last": last_loss, "eval_ids": eval_n, "topk": k,
-        "plain_per_sequence": {"ms": ms_plain, "sequences_per_s": eval_n / (ms_plain * 1e-3)},
-        "learned_pruned": res["trained"], "untrained_pruned": res["untrained"],
-    }
+    return res
+
+
+def learned_full_space(hp, s, torch, net, phen, k: int = 4, chunk: int = 1 << 20):
+    """The learned + pruned form over EVERY id of the box, compared with the exhaustive map `phen`;
+    CUDA events around each chunk's proposal + expansion + pruned scan (the id ranges are made and the
+    comparison is done outside them)."""
+    total = 1 << s.N
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    mism = torch.zeros((), dtype=torch.int64, device="cuda")
+    evs = []
+    for off in range(0, total, chunk):
+        ids = torch.arange(off, min(off + chunk, total), dtype=torch.int64, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        cand = hp.proposal_conformations(s, net.topk(ids, k))
+        got = hp.sequence_scan(s, ids, cand=cand, counters=cnt)
+        b.record()
+        evs.append((a, b))
+        mism += (got != phen[off:off + ids.numel()]).sum()
+    torch.cuda.synchronize()
+    net.status()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    return {"ids": total, "ms": ms, "sequences_per_s": total / (ms * 1e-3),
+            "exact_eval_fraction": int(cnt[0]) / (total * s.S_dir), "mismatches_vs_exhaustive_map": int(mism.item())}
+
+
+def learned_leg(hp, s, torch, full_space: bool = True, eval_n: int = 1 << 16, k: int = 4):
+    """3x3x3: labels = the lowest-index minimiser (aux output) of the exhaustive kernel's full map on the
+    seeded 1-in-10 sample of the space; evaluation on `eval_n` seeded ids and on the whole space."""
+    from paper_2008_05612_gb300 import inputs
+
+    N = s.N
+    phen = torch.empty(1 << N, dtype=torch.int32, device="cuda")
+    aux = torch.empty(1 << N, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hp.phenotype_map(s, 0, 1 << N, out=phen, aux=aux)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_map = e0.elapsed_time(e1)
+    ids_all = np.arange(1 << N, dtype=np.uint64)
+    train_ids = ids_all[inputs.training_mask(ids_all)]
+    del ids_all
+    tids = torch.from_numpy(train_ids.view(np.int64)).to("cuda")
+    tlab = aux[tids]
+    del aux
+    net, untrained, info = train_proposal(hp, s, torch, tids, tlab)
+    del tids, tlab
+    ev = torch.from_numpy(inputs.sample_ids(N, eval_n, seed=123).view(np.int64)).to("cuda")
+    res = compare_on_ids(hp, s, torch, ev, {"learned_pruned": net, "untrained_pruned": untrained}, k)
+    out = {"box": "3x3x3", "labels": "aux output of the exhaustive map kernel, seeded 1-in-10 sample of the space", **info,
+           "eval_ids": eval_n, "eval": "inputs.sample_ids(27, 65536, seed=123)", "topk": k, **res,
+           "exhaustive_map": {"ms": ms_map, "sequences_per_s": (1 << N) / (ms_map * 1e-3)}}
+    if full_space:
+        out["full_space"] = learned_full_space(hp, s, torch, net, phen, k)
+    return out
+
+
+def learned_leg_6x6(hp, torch, n_train: int = 13_421_773, eval_per_shard: int = 1 << 15, shards: int = 2, k: int = 4):
+    """6x6 (N = 36, the paper's Table 3 sampling workload): labels = the lowest-index minimiser from the plain
+    per-sequence scan on seeded uniform ids (the evaluation draws uniform ids, so the training ids do too);
+    evaluation on `eval_per_shard` seeded ids of each of `shards` seeded 2^32-id shards (shard k = the top 4
+    bits), plain scan vs learned + pruned."""
+    from paper_2008_05612_gb300 import inputs
+
+    s = hp.Structs((6, 6))
+    N = s.N
+    tids = torch.from_numpy(inputs.sample_ids(N, n_train, seed=611).view(np.int64)).to("cuda")
+    tlab = torch.empty(n_train, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for off in range(0, n_train, 1 << 20):
+        _, a = hp.sequence_scan(s, tids[off:off + (1 << 20)], aux=True)
+        tlab[off:off + a.numel()] = a
+    e1.record()
+    torch.cuda.synchronize()
+    label_ms = e0.elapsed_time(e1)
+    net, untrained, info = train_proposal(hp, s, torch, tids, tlab)
+    del tids, tlab
+    parts, kk = [], []
+    for j in range(shards):
+        kj = inputs.shard_index(j)
+        kk.append(kj)
+        low = inputs.sample_ids(32, eval_per_shard, seed=700 + j)
+        parts.append(low | (np.uint64(kj) << np.uint64(32)))
+    ev = torch.from_numpy(np.concatenate(parts).view(np.int64)).to("cuda")
+    res = compare_on_ids(hp, s, torch, ev, {"learned_pruned": net, "untrained_pruned": untrained}, k)
+    return {"box": "6x6", "labels": f"aux output of the plain per-sequence scan on {n_train} seeded uniform ids",
+            "label_ms": label_ms, **info, "eval_ids": int(ev.numel()),
+            "eval": f"{eval_per_shard} seeded ids in each of the shards {kk} (inputs.shard_index(j), j < {shards})",
+            "topk": k, **res}
 
 
 def main():
@@ -401,16 +509,14 @@ def main():
     s = hp.Structs(DIMS)
     N, S, Sdir = s.N, s.S, s.S_dir
     if args.learned_only:
-        print(json.dumps({"metric": METRIC, "learned": learned_leg(hp, s, torch)}))
+        print(json.dumps({"metric": METRIC, "learned": {"3x3x3": learned_leg(hp, s, torch),
+                                                         "6x6": learned_leg_6x6(hp, torch)}}))
         return 0
     if args.train_case:
         from paper_2008_05612_gb300 import inputs
 
-        params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
-                  inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
-                  inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
         batch = 4096
-        net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
+        net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, proposal_params(N, S))
         ids_np = inputs.sample_ids(N, batch * 8, seed=321)
         ids = torch.from_numpy(ids_np.view(np.int64)).cuda()
         labels = torch.from_numpy((inputs.splitmix64(ids_np) % np.uint64(S)).astype(np.int32)).cuda()
@@ -435,10 +541,7 @@ def main():
     if args.proposal_case:
         from paper_2008_05612_gb300 import inputs
 
-        params = [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
-                  inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
-                  inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
-        net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
+        net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, proposal_params(N, S))
         ev = torch.from_numpy(inputs.sample_ids(N, 1 << 16, seed=123).view(np.int64)).cuda()
         for _ in range(args.warmup):
             net.topk(ev, 4)
@@ -572,11 +675,15 @@ def main():
                              "map kernel's CUDA-event time inside the step"},
         "clocks": clocks,
     }
+    if rank == 0:
+        line["box_6x6"] = map_block_6x6(hp, torch, peak_ops)
     if rank == 0 and not args.no_learned:
-        try:
-            line["learned"] = learned_leg(hp, s, torch)
-        except Exception as exc:  # reported in the line, never hides the main measurement
-            line["learned"] = {"error": f"{type(exc).__name__}: {exc}"}
+        line["learned"] = {}
+        for name, fn in (("3x3x3", lambda: learned_leg(hp, s, torch)), ("6x6", lambda: learned_leg_6x6(hp, torch))):
+            try:
+                line["learned"][name] = fn()
+            except Exception as exc:  # reported in the line, never hides the main measurement
+                line["learned"][name] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(DIMS)
     if rank == 0:

@@ -26,10 +26,19 @@
  *     the lexicographically smallest tuple (site(r_0), ..., site(r_{N-1})),
  *     site = x + Lx*(y + Ly*z), over G and both directions.
  *   - Device pointers are plain CUDA device addresses owned by the caller;
- *     `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
- *     is stream-ordered and returns as soon as its work is enqueued, except
- *     where stated.  No call aborts the process; each returns an hp_status
- *     and leaves a message for hp_last_error().
+ *     `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     stream-ordered.  Calls that check a device-side error word read it back
+ *     and therefore SYNCHRONISE their stream before returning: the map calls
+ *     (hp_phenotype_map, hp_phenotype_map_batch, hp_autotune), the map
+ *     reductions (hp_designability, hp_designability_noalloc,
+ *     hp_robustness, hp_neighbourhood, hp_phi_matrix, hp_robustness_cross,
+ *     hp_neutral_components), hp_stream_shards, hp_batch_plan_status,
+ *     hp_mlp_status, and the network calls that read a value back.  The
+ *     others (hp_sequence_scan, hp_sequence_scan_gap, hp_mlp_topk,
+ *     hp_mlp_logits, hp_proposal_conformations after its first call,
+ *     hp_batch_plan_launch) return as soon as their work is enqueued.  No
+ *     call aborts the process; each returns an hp_status and leaves a
+ *     message for hp_last_error().
  */
 #ifndef HP_GPMAP_H
 #define HP_GPMAP_H
@@ -88,7 +97,9 @@ void hp_structs_free(hp_structs* s);
  *                  the lowest-index conformation reaching the minimum energy,
  *                  tied or not (training labels for the learned proposal).
  * seq_begin + seq_count must not exceed 2^N.  Allocates a small stream-
- * ordered scratch block (work counter and error word) per call. */
+ * ordered scratch block (work counter and error word) per call and
+ * synchronises `stream` (it reads the error word back: HP_ETIMEOUT when a
+ * bounded device wait gave up, see hp_set_wait_limit). */
 int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_t seq_count, int32_t gap_threshold,
                      int32_t* d_phen, int32_t* d_argmin_aux, void* stream);
 
@@ -238,8 +249,8 @@ int hp_proposal_conformations(const hp_structs* s, const int32_t* d_top, int64_t
 /* Designability (Section 2.3): d_hist[p] = #{k : d_phen[k] = p} for
  * p in [0, S), d_hist[S] = #{k : d_phen[k] = -1}.
  *   d_phen: device int32[count], entries in [-1, S); d_hist: device
- *   uint64[S + 1], overwritten.  Entries outside [-1, S) set HP_EINVAL at the
- *   next synchronising call of this library (they are counted nowhere). */
+ *   uint64[S + 1], overwritten.  Synchronises `stream`: entries outside
+ *   [-1, S) are counted nowhere and make the call return HP_EINVAL. */
 int hp_designability(const int32_t* d_phen, uint64_t count, int32_t S, uint64_t* d_hist, void* stream);
 
 /* Designability without any device allocation: the same result as
@@ -265,7 +276,8 @@ int hp_designability_noalloc(const int32_t* d_phen, uint64_t count, int32_t S, u
  *   d_to_del[p]  = sum over g with P(g) = p of #{i : P(g xor 2^i) = -1}
  * for p in [0, S); index S stands for the deleterious phenotype.  Robustness
  * rho_p = d_neutral[p] / (N * N_p) and phi_del = d_to_del[p] / (N * N_p).
- *   d_phen: device int32[2^N]; d_neutral, d_to_del: device uint64[S + 1]. */
+ *   d_phen: device int32[2^N]; d_neutral, d_to_del: device uint64[S + 1].
+ * Synchronises `stream` (error word: HP_EINVAL for entries outside [-1, S)). */
 int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64_t* d_neutral, uint64_t* d_to_del,
                   void* stream);
 
@@ -273,14 +285,36 @@ int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64_t* d_neutr
  * allowed) d_row[p] = sum over g with P(g) = q of #{i : P(g xor 2^i) = p},
  * index S for -1; phi_pq = d_row[p] / (N * N_q).  This is the neighbourhood
  * of the top fold analysed in Section 3.2 (Figure 7).
- *   d_phen: device int32[2^N]; d_row: device uint64[S + 1], overwritten. */
+ *   d_phen: device int32[2^N]; d_row: device uint64[S + 1], overwritten.
+ * Synchronises `stream`. */
 int hp_neighbourhood(const int32_t* d_phen, int32_t N, int32_t S, int32_t q, uint64_t* d_row, void* stream);
+
+/* The whole matrix of Eq. 2 numerators over a FULL map of 2^N sequences
+ * (Section 2.3, Eq. 2; the null-model comparison of Eq. 3 and Section 3.2
+ * reads it): for every ordered pair of phenotypes (q, p), index S for -1,
+ *   M[q][p] = #{(g, i) : P(g) = q, P(g xor 2^i) = p},
+ * so phi_pq = M[q][p] / (N N_q), rho_q = M[q][q], phi_del = M[q][S] / (N N_q).
+ * Output in compressed rows, only the nonzero entries, columns ascending:
+ *   d_row_ptr: device uint64[S + 2]; row q is entries [d_row_ptr[q],
+ *              d_row_ptr[q + 1]); d_row_ptr[S + 1] = nnz;
+ *   d_col:     device int32[cap] column p of each entry (S for -1);
+ *   d_count:   device uint64[cap] M[q][p] of each entry;
+ *   *h_nnz:    host; the number of nonzero entries.
+ *   d_phen: device int32[2^N], S in [1, 65534], cap in [1, 2^30].
+ * When the matrix has more than cap nonzero entries, returns HP_ENOMEM with
+ * *h_nnz = the number needed (0 if the count itself overflowed its table of
+ * 2 cap slots: retry with a larger cap) and writes no output.  Allocates a
+ * stream-ordered scratch block of about 12 x 2 cap + 12 x cap bytes;
+ * synchronises `stream` (it reads the entry count back). */
+int hp_phi_matrix(const int32_t* d_phen, int32_t N, int32_t S, uint64_t cap, uint64_t* d_row_ptr, int32_t* d_col,
+                  uint64_t* d_count, uint64_t* h_nnz, void* stream);
 
 /* Eq. 2 numerators across one high bit between two equally sized aligned
  * blocks: genotype base_a + x of block A flips to base_b + x of block B.
  * ADDS to d_neutral[P_A(x)] when P_B(x) = P_A(x) and to d_to_del[P_A(x)]
  * when P_B(x) = -1 (index S for -1, where both rows count -1 -> -1).
- * Used by the shard streamer for flips between shards. */
+ * Used by the shard streamer for flips between shards.  Synchronises
+ * `stream`. */
 int hp_robustness_cross(const int32_t* d_phen_a, const int32_t* d_phen_b, uint64_t count, int32_t S,
                         uint64_t* d_neutral, uint64_t* d_to_del, void* stream);
 
@@ -305,12 +339,28 @@ int hp_stream_shards(const hp_structs* s, int32_t shard_bits, int32_t window, co
  *   d_phen:  device int32[2^N], N <= 31;
  *   d_label: device int32[2^N]; d_label[g] = smallest id in g's component,
  *            -1 where P(g) = -1;
- *   d_ncomp: device uint64[S]; number of components of each phenotype. */
+ *   d_ncomp: device uint64[S]; number of components of each phenotype.
+ * Synchronises `stream` (HP_ETIMEOUT if a union's bounded retries ran out). */
 int hp_neutral_components(const int32_t* d_phen, int32_t N, int32_t S, int32_t* d_label, uint64_t* d_ncomp,
                           void* stream);
 
 /* Thread-local text of the last failure in this library (never NULL). */
 const char* hp_last_error(void);
+
+/* Failure-detection hook (no counterpart in the paper).  Every wait of the
+ * map kernel and of the tcgen05 GEMM on a shared-memory barrier is bounded:
+ * after a number of polls it gives up, the kernel records the timeout in its
+ * device error word, stops, waits (with a fixed bound of its own) for the
+ * copies and tensor-core operations it still has in flight, and returns, and
+ * the call reports HP_ETIMEOUT (hp_phenotype_map, the batch and plan calls,
+ * hp_autotune) or hp_mlp_status does.  This call sets the poll limit of those
+ * waits for every later launch in the process: polls >= 0 sets it (0 gives
+ * up at the first check, which lets a test see the timeout path end in
+ * HP_ETIMEOUT with the context still usable), polls < 0 restores each
+ * kernel's built-in limit.  The exit drains keep their fixed limit.  It is a
+ * process-wide setting for tests: launches made while it is lowered fail.
+ * Graph plans keep the limit they were created with.  Always HP_OK. */
+int hp_set_wait_limit(int64_t polls);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ EXPORTS = (
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
     "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
     "hp_batch_plan_free", "hp_sequence_scan", "hp_sequence_scan_gap", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
-    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_robustness_cross", "hp_stream_shards",
+    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_phi_matrix", "hp_robustness_cross", "hp_stream_shards",
     "hp_neutral_components",
     "hp_last_error", "hp_set_wait_limit",
 )
@@ -91,6 +91,7 @@ def lib():
         L.hp_robustness.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_neutral_components.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_neighbourhood.argtypes = [vp, i32, i32, i32, vp, vp]
+        L.hp_phi_matrix.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
         L.hp_robustness_cross.argtypes = [vp, vp, u64, i32, vp, vp, vp]
         L.hp_stream_shards.argtypes = [vp, i32, i32, ctypes.c_char_p, vp, vp, vp, vp, vp]
         L.hp_last_error.restype = ctypes.c_char_p
@@ -430,6 +431,31 @@ def neighbourhood(phen, N: int, S: int, q: int, stream=None):
     _check(lib().hp_neighbourhood(_dptr(phen, torch.int32, "phen"), N, S, q, _dptr(row, torch.int64, "row"),
                                   _stream_ptr(stream)))
     return row
+
+
+def phi_matrix(phen, N: int, S: int, cap: int | None = None, stream=None):
+    """The Eq. 2 numerator matrix in compressed rows (hp_phi_matrix): (row_ptr int64[S+2], col int32[nnz],
+    count int64[nnz]); row and column S stand for -1.  cap: output capacity, grown and retried when
+    the call reports that the matrix is larger."""
+    import torch
+
+    if phen.numel() != (1 << N):
+        raise ValueError("the phi matrix needs the full map of 2^N sequences")
+    cap = int(cap or max(1 << 16, 8 * (S + 1)))
+    pp = _dptr(phen, torch.int32, "phen")
+    row_ptr = torch.empty(S + 2, dtype=torch.int64, device=phen.device)
+    while True:
+        col = torch.empty(cap, dtype=torch.int32, device=phen.device)
+        count = torch.empty(cap, dtype=torch.int64, device=phen.device)
+        nnz = ctypes.c_uint64(0)
+        with torch.cuda.device(phen.device):
+            rc = lib().hp_phi_matrix(pp, N, S, cap, _dptr(row_ptr, torch.int64, "row_ptr"), _dptr(col, torch.int32, "col"),
+                                     _dptr(count, torch.int64, "count"), ctypes.byref(nnz), _stream_ptr(stream))
+        if rc == HP_ENOMEM and cap < (1 << 30) and "cap" in lib().hp_last_error().decode():
+            cap = min(1 << 30, max(2 * cap, int(nnz.value)))
+            continue
+        _check(rc)
+        return row_ptr, col[: nnz.value], count[: nnz.value]
 
 
 def stream_shards(structs: Structs, shard_bits: int, window: int | None = None, out_dir: str | None = None,

@@ -46,8 +46,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *COMMON, "-c", src, "-o", obj]
-        if src.endswith(".cpp"):
-            cmd[1:1] = ["-x", "cu"] if False else []
         if verbose:
             cmd.append("-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -105,11 +105,8 @@ extern "C" int hp_autotune(hp_structs* s, hp_tile_cfg* best, float* ms, void* st
   hp::PhenParams* prm = new (std::nothrow) hp::PhenParams();
   if (!prm) return hp::fail(HP_ENOMEM, "hp_autotune: out of host memory");
   int32_t* scratch = nullptr;
-  unsigned* ctrl = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, sizeof(int32_t) * (size_t)count, st);
-  if (e == cudaSuccess) e = cudaMallocAsync(&ctrl, hp::kPhenCtrlBytes, st);
   if (e != cudaSuccess) {
-    if (scratch) cudaFreeAsync(scratch, st);
     delete prm;
     return hp::cuda_fail(e, "hp_autotune: cudaMallocAsync");
   }
@@ -118,16 +115,30 @@ extern "C" int hp_autotune(hp_structs* s, hp_tile_cfg* best, float* ms, void* st
   cudaEventCreate(&e1);
   float best_ms = 0;
   int best_i = -1, rc = HP_OK;
+  unsigned herr = 0;
   const hp_structs* cs = s;
   for (int i = 0; i < kNumShapes && rc == HP_OK; i++) {
     rc = hp::plan_phenotype(&cs, &begin, &count, 1, &scratch, nullptr, kShapes[i][1], *prm);
     if (rc != HP_OK) break;
     const unsigned long long limit = 2ull * grid;
     if (prm->total_items > limit) prm->total_items = limit;
-    prm->ctrl = ctrl;
-    float t_ms = 0;
+    float t_ms = -1;
+    size_t bytes = 0;
+    unsigned ctas = 0;
+    void* block = nullptr;
+    if (hp::launch_block_bytes(*prm, kShapes[i][0], kShapes[i][1], grid, &bytes, &ctas) != HP_OK) {
+      // a shape that does not fit this device is skipped, not fatal
+      if (ms) ms[i] = -1;
+      continue;
+    }
+    e = cudaMallocAsync(&block, bytes, st);
+    if (e != cudaSuccess) {
+      rc = hp::cuda_fail(e, "hp_autotune: cudaMallocAsync(control words and work lists)");
+      break;
+    }
+    hp::bind_launch_block(*prm, block, ctas);
     for (int rep = 0; rep < 2 && rc == HP_OK; rep++) {  // first run warms up
-      cudaMemsetAsync(ctrl, 0, hp::kPhenCtrlBytes, st);
+      cudaMemsetAsync(prm->ctrl, 0, hp::kPhenCtrlBytes, st);
       cudaEventRecord(e0, st);
       rc = hp::launch_phenotype(*prm, kShapes[i][0], kShapes[i][1], st, grid);
       cudaEventRecord(e1, st);
@@ -135,29 +146,25 @@ extern "C" int hp_autotune(hp_structs* s, hp_tile_cfg* best, float* ms, void* st
         e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_autotune: timing run");
         cudaEventElapsedTime(&t_ms, e0, e1);
-      } else if (hp::tile_cfg_supported(kShapes[i][0], kShapes[i][1])) {
-        // a shape that does not fit this device is skipped, not fatal
-        rc = HP_OK;
-        t_ms = -1;
-        break;
       }
     }
+    if (rc == HP_OK) {
+      unsigned h = 0;
+      e = cudaMemcpyAsync(&h, prm->ctrl, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_autotune");
+      herr |= h;
+    }
+    cudaFreeAsync(block, st);
     if (ms) ms[i] = t_ms;
     if (rc == HP_OK && t_ms > 0 && (best_i < 0 || t_ms < best_ms)) {
       best_ms = t_ms;
       best_i = i;
     }
   }
-  unsigned herr = 0;
-  if (rc == HP_OK) {
-    e = cudaMemcpyAsync(&herr, ctrl, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_autotune");
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFreeAsync(scratch, st);
-  cudaFreeAsync(ctrl, st);
   delete prm;
   if (rc != HP_OK) return rc;
   if (herr) return hp::fail(HP_ETIMEOUT, "hp_autotune: a timing run reported a device-side timeout");
@@ -190,7 +197,17 @@ extern "C" int hp_batch_plan_create(const hp_structs* const* libs, const uint64_
   // tables are uploaded here, before capture begins
   rc = hp::plan_phenotype(libs, begins, counts, n, d_phen, nullptr, t, *prm);
   cudaError_t e = cudaSuccess;
-  if (rc == HP_OK) {
+  if (rc == HP_OK && prm->total_items) {
+    cudaGetDevice(&plan->device);
+    size_t bytes = 0;
+    unsigned ctas = 0;
+    rc = hp::launch_block_bytes(*prm, r, t, 0, &bytes, &ctas);
+    if (rc == HP_OK) {
+      e = cudaMalloc(&plan->ctrl, bytes);
+      if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaMalloc");
+      else hp::bind_launch_block(*prm, plan->ctrl, ctas);
+    }
+  } else if (rc == HP_OK) {
     cudaGetDevice(&plan->device);
     e = cudaMalloc(&plan->ctrl, hp::kPhenCtrlBytes);
     if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaMalloc");
@@ -201,7 +218,6 @@ extern "C" int hp_batch_plan_create(const hp_structs* const* libs, const uint64_
     if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaStreamCreate");
   }
   if (rc == HP_OK) {
-    prm->ctrl = plan->ctrl;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaMemsetAsync(plan->ctrl, 0, hp::kPhenCtrlBytes, cap);

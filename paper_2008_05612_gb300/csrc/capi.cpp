@@ -1,6 +1,7 @@
 // Status handling and per-device tables shared by the C entry points.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
@@ -9,6 +10,7 @@
 
 namespace {
 thread_local std::string g_last_error = "no error";
+std::atomic<long long> g_wait_limit{-1};  // < 0: every kernel uses its own constant
 }
 
 namespace hp {
@@ -21,6 +23,11 @@ int fail(int code, const std::string& msg) {
 int cuda_fail(int err, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString((cudaError_t)err);
   return err == cudaErrorMemoryAllocation ? HP_ENOMEM : HP_ECUDA;
+}
+
+long long wait_limit(long long dflt) {
+  const long long v = g_wait_limit.load(std::memory_order_relaxed);
+  return v < 0 ? dflt : v;
 }
 
 int device_tables(const hp_structs* cs, DevTables** out) {
@@ -71,6 +78,11 @@ int device_tables(const hp_structs* cs, DevTables** out) {
 }  // namespace hp
 
 extern "C" const char* hp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int hp_set_wait_limit(int64_t polls) {
+  g_wait_limit.store(polls < 0 ? -1 : (long long)polls, std::memory_order_relaxed);
+  return HP_OK;
+}
 
 extern "C" void hp_structs_free(hp_structs* s) {
   if (!s) return;

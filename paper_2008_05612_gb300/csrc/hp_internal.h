@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of libhp_gpmap.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -81,4 +83,11 @@ int scan_tables(const hp_structs* s, DevTables** out);
 int half_tables(const hp_structs* s, DevTables** out);
 // Records are padded on the device to a multiple of this many conformations.
 constexpr int kRecPad = 256;
+// Poll limit for the bounded device-side waits of the kernels: `dflt` (the kernel's own
+// constant) unless hp_set_wait_limit has set a limit for this process.
+long long wait_limit(long long dflt);
+// Eq. 2 numerators of a full 2^N map (robustness tile pass): ADDS to neutral / to_del [S + 1] and
+// counts the -1 genotypes into *negcount (all caller-zeroed); error bits go to *err.
+cudaError_t launch_robustness(const int32_t* d_phen, int N, int S, unsigned long long* neutral,
+                              unsigned long long* to_del, unsigned long long* negcount, unsigned* err, cudaStream_t st);
 }  // namespace hp

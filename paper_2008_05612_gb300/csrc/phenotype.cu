@@ -49,6 +49,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "hp_internal.h"
@@ -59,7 +60,8 @@ namespace {
 constexpr int kLaneRoles = 5;
 constexpr int kRoles = 14;  // even-pattern bits covered by one CTA
 constexpr unsigned kErrTimeout = 1u;
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr unsigned kErrDrain = 2u;  // the exit drain gave up with bulk copies in flight
+constexpr long long kSpinLimit = 1ll << 26;  // polls of the exit drain (fixed); the other waits take PhenParams::spin
 
 __device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
   uint32_t d;
@@ -139,7 +141,10 @@ struct Cfg {
   static constexpr int CS_RAW = TP_OFF + TP_WORDS;
   // words per record: a multiple of 4 that is odd in 16-byte units (conflict-free 16-byte stores)
   static constexpr int CSTRIDE = ((CS_RAW / 4) % 2 == 1) ? CS_RAW : CS_RAW + 4;
-  static constexpr int kCoefWords = 2 * T * CSTRIDE;
+  // pass 2 reads word j of 32 consecutive records (one per lane): an odd stride in words keeps
+  // those loads conflict-free, and the records are written with 4-byte stores
+  static constexpr int CS2 = CS_RAW | 1;
+  static constexpr int kCoefWords = 2 * T * (CSTRIDE > CS2 ? CSTRIDE : CS2);
   static constexpr int kStateWords = 2 * P * THREADS;
   static_assert(T <= THREADS, "one producer thread per conformation of a tile");
   static_assert(T % 32 == 0 && hp::kRecPad % T == 0, "tiles are whole warps and tile the padded table");
@@ -147,24 +152,26 @@ struct Cfg {
 };
 
 // Turn tile t's staged records (bulk copy issued two tiles ahead) into this CTA's coefficient
-// records in buffer t & 1: one thread per conformation.  No barrier: the caller's next CTA barrier
-// publishes the records; a bounded wait that gives up raises *s_abort.
-template <class K>
+// records in buffer t & 1: one thread per conformation.  P2: the pass-2 layout (stride CS2, 4-byte
+// stores) instead of pass 1's (stride CSTRIDE, 16-byte stores).  No barrier: the caller publishes
+// the records (mbarrier arrive); a bounded wait that gives up raises *s_abort.
+template <class K, bool P2 = false>
 __device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* err, int t, uint32_t* rawbuf,
                                              uint32_t* coefbuf, uint64_t* bars,
                                              unsigned (&waited)[2], uint32_t o, uint32_t ehigh, int nroles,
-                                             int* s_abort) {
+                                             int* s_abort, long long spin) {
   constexpr int R = K::R, T = K::T;
   const int tid = threadIdx.x;
   const int buf = t & 1;
-  uint32_t* cbuf = coefbuf + buf * T * K::CSTRIDE;
+  constexpr int STRIDE = P2 ? K::CS2 : K::CSTRIDE;
+  uint32_t* cbuf = coefbuf + buf * T * STRIDE;
   if (tid < T) {
-    if (!mbar_wait(&bars[buf], waited[buf] & 1u)) {
+    if (!mbar_wait(&bars[buf], waited[buf] & 1u, spin)) {
       atomicOr(err, kErrTimeout);
       *s_abort = 1;
     } else {
       const uint32_t* r = rawbuf + buf * T * in.rec_words + tid * in.rec_words;
-      uint32_t* c = cbuf + tid * K::CSTRIDE;
+      uint32_t* c = cbuf + tid * STRIDE;
       const int s = t * T + tid;
       if (s < in.S_dir) {
         uint32_t a[kRoles];
@@ -183,10 +190,15 @@ __device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* e
           const int hb = 31 - __clz(l);
           lt[l] = lt[l ^ (1 << hb)] + a[R + hb];
         }
+        if (P2) {
 #pragma unroll
-        for (int l = 0; l < 32; l += 4)
-          *reinterpret_cast<uint4*>(c + l) = make_uint4(lt[l] * 0x10001u + split_hi, lt[l + 1] * 0x10001u + split_hi,
-                                                        lt[l + 2] * 0x10001u + split_hi, lt[l + 3] * 0x10001u + split_hi);
+          for (int l = 0; l < 32; l++) c[l] = lt[l] * 0x10001u + split_hi;
+        } else {
+#pragma unroll
+          for (int l = 0; l < 32; l += 4)
+            *reinterpret_cast<uint4*>(c + l) = make_uint4(lt[l] * 0x10001u + split_hi, lt[l + 1] * 0x10001u + split_hi,
+                                                          lt[l + 2] * 0x10001u + split_hi, lt[l + 3] * 0x10001u + split_hi);
+        }
         uint32_t wt[K::NW];
         wt[0] = 0;
 #pragma unroll
@@ -194,45 +206,36 @@ __device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* e
           const int hb = 31 - __clz(w);
           wt[w] = wt[w ^ (1 << hb)] + a[R + kLaneRoles + hb];
         }
-#pragma unroll
-        for (int w = 0; w < K::NW; w += 4)
-          *reinterpret_cast<uint4*>(c + K::WT_OFF + w) =
-              make_uint4(wt[w] * 0x10001u, wt[w + 1] * 0x10001u, wt[w + 2] * 0x10001u, wt[w + 3] * 0x10001u);
         uint32_t tp[K::TP_WORDS];
 #pragma unroll
         for (int j = 0; j < K::TP_WORDS; j++) tp[j] = j < R - 1 ? a[1 + j] * 0x10001u : 0u;
+        if (P2) {
 #pragma unroll
-        for (int j = 0; j < K::TP_WORDS; j += 4)
-          *reinterpret_cast<uint4*>(c + K::TP_OFF + j) = make_uint4(tp[j], tp[j + 1], tp[j + 2], tp[j + 3]);
+          for (int w = 0; w < K::NW; w++) c[K::WT_OFF + w] = wt[w] * 0x10001u;
+#pragma unroll
+          for (int j = 0; j < R - 1; j++) c[K::TP_OFF + j] = tp[j];
+        } else {
+#pragma unroll
+          for (int w = 0; w < K::NW; w += 4)
+            *reinterpret_cast<uint4*>(c + K::WT_OFF + w) =
+                make_uint4(wt[w] * 0x10001u, wt[w + 1] * 0x10001u, wt[w + 2] * 0x10001u, wt[w + 3] * 0x10001u);
+#pragma unroll
+          for (int j = 0; j < K::TP_WORDS; j += 4)
+            *reinterpret_cast<uint4*>(c + K::TP_OFF + j) = make_uint4(tp[j], tp[j + 1], tp[j + 2], tp[j + 3]);
+        }
       } else {
         // padding conformation: every score 0, below every real (biased) score
+        if (P2) {
 #pragma unroll
-        for (int k = 0; k < K::CS_RAW; k += 4) *reinterpret_cast<uint4*>(c + k) = make_uint4(0, 0, 0, 0);
+          for (int k = 0; k < K::CS_RAW; k++) c[k] = 0u;
+        } else {
+#pragma unroll
+          for (int k = 0; k < K::CS_RAW; k += 4) *reinterpret_cast<uint4*>(c + k) = make_uint4(0, 0, 0, 0);
+        }
       }
     }
   }
   waited[buf]++;
-}
-
-// produce_work for tile t, then a CTA barrier and the bulk copy of tile t + 2 into the raw buffer
-// it has just freed; returns false if a bounded wait gave up.
-template <class K>
-__device__ __forceinline__ bool produce_tile(const hp::PhenInst& in, unsigned* err, int t, uint32_t* rawbuf,
-                                             uint32_t* coefbuf, uint64_t* bars, unsigned (&issued)[2],
-                                             unsigned (&waited)[2], uint32_t o, uint32_t ehigh, int nroles,
-                                             int* s_abort) {
-  constexpr int T = K::T;
-  produce_work<K>(in, err, t, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, s_abort);
-  __syncthreads();
-  if (*s_abort) return false;
-  const int buf = t & 1;
-  if (t + 2 < in.ntiles) {
-    if (threadIdx.x == 0)
-      bulk_load(rawbuf + buf * T * in.rec_words, in.rec + (size_t)(t + 2) * T * in.rec_words,
-                (unsigned)(T * in.rec_words * 4), &bars[buf]);
-    issued[buf]++;
-  }
-  return true;
 }
 
 template <int T>
@@ -318,25 +321,28 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     // written, every warp arrives on empty[b] when it has consumed it, and a warp waits only for
     // the buffer it needs next, so fast warps run ahead instead of idling at a barrier.
     const bool producer = tid < T;
-    auto produce_and_publish = [&](int tp) {
+    auto produce_and_publish = [&](int tp, auto p2) {
       const int b = tp & 1;
       if (producer) {
         // the previous contents of buffer b (tile tp - 2) must have been consumed by every warp
-        if (tp >= 2 && !mbar_wait(&bars[4 + b], ((b ? ccnt1 : ccnt0) - 1u) & 1u, 1ll << 22)) {
+        if (tp >= 2 && !mbar_wait(&bars[4 + b], ((b ? ccnt1 : ccnt0) - 1u) & 1u, p.spin_handover)) {
           atomicOr(p.ctrl, kErrTimeout);
           s_abort = 1;
         }
       }
-      produce_work<K>(in, p.ctrl, tp, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort);
+      produce_work<K, decltype(p2)::value>(in, p.ctrl, tp, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort,
+                                           p.spin);
       if (producer) {
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bars[2 + b])) : "memory");
       }
     };
-    produce_and_publish(0);
+    using Pass1Layout = std::false_type;
+    using Pass2Layout = std::true_type;
+    produce_and_publish(0, Pass1Layout{});
     for (int t = 0; t < in.ntiles; t++) {
       const int b = t & 1;
-      if (!mbar_wait(&bars[2 + b], (b ? fcnt1 : fcnt0) & 1u, 1ll << 22)) {
+      if (!mbar_wait(&bars[2 + b], (b ? fcnt1 : fcnt0) & 1u, p.spin_handover)) {
         atomicOr(p.ctrl, kErrTimeout);
         s_abort = 1;
       }
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         }
       };
       consume(0, T / 2);
-      if (t + 1 < in.ntiles) produce_and_publish(t + 1);
+      if (t + 1 < in.ntiles) produce_and_publish(t + 1, Pass1Layout{});
       consume(T / 2, T);
       // this warp is done with buffer b
       __syncwarp();
@@ -407,8 +413,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
 
     // ================= classify: a field stays a candidate (best >= 2) only if its
     // minimum was reached in a single tile (or labels are wanted); others resolve to -1
-    // (cmask: bit 2v + h marks an unresolved candidate, so pass 2 visits only those fields)
-    int next_tile = 0x7FFFFFFF;
+    // (cmask: bit 2v + h marks a candidate, which pass 2 resolves)
     unsigned long long cmask = 0;  // 2P <= 64 fields
 #pragma unroll
     for (int v = 0; v < P; v++) {
@@ -429,7 +434,6 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
           mv &= ~(0xFFFFu << (16 * h));
           tv |= 0xFFFFu << (16 * h);
         } else {
-          next_tile = min(next_tile, (int)((tv >> (16 * h)) & 0xFFFFu));
           cmask |= 1ull << (2 * v + h);
         }
       }
@@ -437,71 +441,131 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       st_tile[v * kThreads + tid] = tv;
     }
 
-    // ================= pass 2: re-stage each tile and resolve the candidates whose best lies in it
-    prefetch_first_tiles<T>(in, rawbuf, bars, issued);
-    for (int t = 0; t < in.ntiles; t++) {
-      if (!produce_tile<K>(in, p.ctrl, t, rawbuf, coefbuf, bars, issued, waited, o, ehigh, nroles, &s_abort)) break;
-      if (!__any_sync(0xFFFFFFFFu, next_tile == t)) continue;
-      const uint32_t* cbuf = coefbuf + (t & 1) * T * CSTRIDE;
-      bool need = next_tile == t;
-      while (__any_sync(0xFFFFFFFFu, need)) {
-        int f = -1;
-        uint32_t fld = 0;
-        if (need) {
-          for (unsigned long long m = cmask; m && f < 0; m &= m - 1) {
-            const int c = __ffsll((long long)m) - 1, v = c >> 1, h = c & 1;
-            if (((st_tile[v * kThreads + tid] >> (16 * h)) & 0xFFFFu) == (uint32_t)t) {
-              f = c;
-              fld = (st_best[v * kThreads + tid] >> (16 * h)) & 0xFFFFu;
-            }
-          }
-          if (f < 0) need = false;
-        }
-        uint32_t mask = __ballot_sync(0xFFFFFFFFu, f >= 0);
-        while (mask) {
-          const int src = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const int sf = __shfl_sync(0xFFFFFFFFu, f, src);
-          const uint32_t sfld = __shfl_sync(0xFFFFFFFFu, fld, src);
-          const int v = sf >> 1, h = sf & 1;
-          const uint32_t want = sfld & 0xFFFEu;
-          int count = 0, first = -1;
-          for (int i = 0; i < T; i += 32) {
-            const uint32_t* cs = cbuf + (i + lane) * CSTRIDE;
-            uint32_t x = cs[src] + cs[K::WT_OFF + warp];
+    // ================= pass-2 work list: the CTA's candidates grouped by their best tile, one
+    // 16-bit entry (thread << 6 | field) each, in this CTA's global scratch; counted and placed with
+    // shared-memory atomics in the idle coefficient area.  Every warp then takes a share of each
+    // tile's candidates, whoever owns them, so no warp holds up the others with a long list.
+    uint16_t* wl = p.wlist + (size_t)blockIdx.x * p.wl_stride;
+    uint16_t* woff = wl + (1u << kRoles);  // ntiles + 1 offsets
+    unsigned* whist = coefbuf;
+    for (int i = tid; i <= in.ntiles; i += kThreads) whist[i] = 0u;
+    __syncthreads();
+    for (unsigned long long m = cmask; m; m &= m - 1) {
+      const int c = __ffsll((long long)m) - 1;
+      atomicAdd(&whist[(st_tile[(c >> 1) * kThreads + tid] >> (16 * (c & 1))) & 0xFFFFu], 1u);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // exclusive scan of the tile counts: each lane sums a run of tiles, then a warp scan
+      const int per = (in.ntiles + 32) / 32;
+      const int i0 = lane * per, i1 = min(i0 + per, in.ntiles + 1);
+      unsigned run = 0;
+      for (int i = i0; i < i1; i++) run += whist[i];
+      unsigned incl = run;
 #pragma unroll
-            for (int j = 0; j < R - 1; j++)
-              if ((v >> j) & 1) x += cs[K::TP_OFF + j];
-            const uint32_t xf = (x >> (16 * h)) & 0xFFFFu;
-            const bool match = xf == want;  // padding scores 0 never match
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, match);
-            if (first < 0 && bal) first = t * T + i + __ffs(bal) - 1;
-            if (GAP)  // real conformations (padding is 0) within T of the best, the best included
-              count += __popc(__ballot_sync(0xFFFFFFFFu, xf >= 2u && xf + p.gap2 > want));
-            else
-              count += __popc(bal);
-          }
-          if (lane == src) {
-            cmask &= ~(1ull << sf);
-            const int cls = first >= 0 ? in.conf_class[first] : -1;
-            const bool unique = !(sfld & 1u) && count == 1;
-            const uint32_t sh = 16 * h;
-            st_best[v * kThreads + tid] = (st_best[v * kThreads + tid] & ~(0xFFFFu << sh)) | ((unique ? 1u : 0u) << sh);
-            st_tile[v * kThreads + tid] =
-                (st_tile[v * kThreads + tid] & ~(0xFFFFu << sh)) | (((uint32_t)cls & 0xFFFFu) << sh);
-          }
-          __syncwarp();
-        }
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += y;
       }
-      if (next_tile == t) {
-        next_tile = 0x7FFFFFFF;
-        for (unsigned long long m = cmask; m; m &= m - 1) {
-          const int c = __ffsll((long long)m) - 1;
-          next_tile = min(next_tile, (int)((st_tile[(c >> 1) * kThreads + tid] >> (16 * (c & 1))) & 0xFFFFu));
-        }
+      unsigned at = incl - run;
+      for (int i = i0; i < i1; i++) {
+        const unsigned c = whist[i];
+        woff[i] = (uint16_t)at;
+        whist[i] = at;  // becomes the placement cursor
+        at += c;
       }
     }
+    __syncthreads();
+    for (unsigned long long m = cmask; m; m &= m - 1) {
+      const int c = __ffsll((long long)m) - 1;
+      const unsigned t = (st_tile[(c >> 1) * kThreads + tid] >> (16 * (c & 1))) & 0xFFFFu;
+      wl[atomicAdd(&whist[t], 1u)] = (uint16_t)((tid << 6) | c);
+    }
+    __syncthreads();  // the list and offsets are visible to the CTA; the coefficient area is free again
+    // st_best / st_tile as 16-bit fields: field (v, h) of thread x is halfword 2 (v THREADS + x) + h
+    uint16_t* best16 = reinterpret_cast<uint16_t*>(st_best);
+    uint16_t* tile16 = reinterpret_cast<uint16_t*>(st_tile);
+
+    // ================= pass 2: re-stage each tile and resolve its candidates.  The records of
+    // tile t + 1 are produced (pass-2 layout) before tile t is resolved, with the hand-over of pass 1
+    // (produced / consumed mbarriers).
+    prefetch_first_tiles<T>(in, rawbuf, bars, issued);
+    produce_and_publish(0, Pass2Layout{});
+    for (int t = 0; t < in.ntiles; t++) {
+      const int b = t & 1;
+      if (!mbar_wait(&bars[2 + b], (b ? fcnt1 : fcnt0) & 1u, p.spin_handover)) {
+        atomicOr(p.ctrl, kErrTimeout);
+        s_abort = 1;
+      }
+      if (b) fcnt1++;
+      else fcnt0++;
+      if (s_abort) break;
+      // every producer has read raw[b] (tile t): refill it with tile t + 2
+      if (t + 2 < in.ntiles) {
+        if (tid == 0)
+          bulk_load(rawbuf + b * T * in.rec_words, in.rec + (size_t)(t + 2) * T * in.rec_words,
+                    (unsigned)(T * in.rec_words * 4), &bars[b]);
+        issued[b]++;
+      }
+      if (t + 1 < in.ntiles) produce_and_publish(t + 1, Pass2Layout{});
+      const uint32_t* cbuf = coefbuf + b * T * K::CS2;
+      const int e1 = woff[t + 1];
+      for (int e = woff[t] + warp; e < e1; e += K::NW) {
+        const uint32_t ent = wl[e];
+        const int owner = (int)(ent >> 6), c = (int)(ent & 63u), v = c >> 1, h = c & 1;
+        const int src = owner & 31, wo = owner >> 5;
+        const int fi = 2 * (v * kThreads + owner) + h;
+        const uint32_t sfld = best16[fi];
+        const uint32_t want = sfld & 0xFFFEu;
+        // lane l checks conformations l, l + 32, ... of the tile; the steps are independent
+        int count = 0, first = 0x7FFFFFFF;
+#pragma unroll
+        for (int i = 0; i < T; i += 32) {
+          const uint32_t* cs = cbuf + (i + lane) * K::CS2;
+          uint32_t x = cs[src] + cs[K::WT_OFF + wo];
+#pragma unroll
+          for (int j = 0; j < R - 1; j++)
+            if ((v >> j) & 1) x += cs[K::TP_OFF + j];
+          const uint32_t xf = (x >> (16 * h)) & 0xFFFFu;
+          const uint32_t bal = __ballot_sync(0xFFFFFFFFu, xf == want);  // padding scores 0 never match
+          if (bal) first = min(first, i + __ffs(bal) - 1);
+          if (GAP)  // real conformations (padding is 0) within T of the best, the best included
+            count += __popc(__ballot_sync(0xFFFFFFFFu, xf >= 2u && xf + p.gap2 > want));
+          else
+            count += __popc(bal);
+        }
+        if (lane == 0) {
+          // (index in the tile << 1 | unique) beside the tile; the class is looked up after pass 2,
+          // when the loads of all fields can be in flight together
+          const bool unique = !(sfld & 1u) && count == 1;
+          best16[fi] = first != 0x7FFFFFFF ? (uint16_t)(((uint32_t)first << 1) | (unique ? 1u : 0u)) : (uint16_t)0;
+          if (first == 0x7FFFFFFF) tile16[fi] = 0xFFFFu;
+        }
+      }
+      // this warp is done with buffer b
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bars[4 + b])) : "memory");
+      if (b) ccnt1++;
+      else ccnt0++;
+    }
+    __syncthreads();  // every warp is done with the buffers (the next item's pass 1 refills them)
     if (s_abort) break;
+    // class ids of this thread's fields: (tile, index in the tile) -> conformation -> class, into
+    // the final encoding (st_tile: class or 0xFFFF for none; st_best: 1 where the minimum is unique)
+#pragma unroll 4
+    for (int v = 0; v < P; v++) {
+      const uint32_t mv = st_best[v * kThreads + tid], tv = st_tile[v * kThreads + tid];
+      uint32_t nb = 0u, nt = 0u;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const uint32_t tf = (tv >> (16 * h)) & 0xFFFFu, bf = (mv >> (16 * h)) & 0xFFFFu;
+        const uint32_t cls = tf == 0xFFFFu ? 0xFFFFu : (uint32_t)in.conf_class[tf * T + (bf >> 1)] & 0xFFFFu;
+        nt |= cls << (16 * h);
+        nb |= (bf & 1u) << (16 * h);
+      }
+      st_best[v * kThreads + tid] = nb;
+      st_tile[v * kThreads + tid] = nt;
+    }
 
     // reversal mirror of this item's ids (only for non-palindromic odd patterns); when every free
     // even residue is a role of this CTA, the mirrored ids are written in a second, coalesced pass
@@ -597,11 +661,16 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     }
     // the state area and s_item are rewritten by the next item (barriers at its top)
   }
-  // after an abort, wait (bounded) for bulk copies still in flight before exiting
+  // after an abort, wait (with the fixed bound) for bulk copies still in flight before exiting; a
+  // copy that does not land in time may still write into shared memory that a later CTA owns, so
+  // that is reported as its own error and the host treats the whole launch as invalid
   if (tid == 0) {
     for (int k = 0; k < 2; k++)
       while (waited[k] < issued[k]) {
-        if (!mbar_wait(&bars[k], waited[k] & 1u)) break;
+        if (!mbar_wait(&bars[k], waited[k] & 1u, kSpinLimit)) {
+          atomicOr(p.ctrl, kErrDrain);
+          break;
+        }
         waited[k]++;
       }
   }
@@ -613,8 +682,11 @@ size_t smem_bytes(int max_rec_words) {
   return words * 4 + 6 * sizeof(uint64_t);
 }
 
+// Grid of a launch of this shape (one wave of resident CTAs, at most one per work item), and with
+// `launch` set the launch itself.
 template <class K, bool GAP = false>
-int launch_shape(const hp::PhenParams& prm, cudaStream_t stream, unsigned grid_limit) {
+int shape_grid_or_launch(const hp::PhenParams& prm, cudaStream_t stream, unsigned grid_limit, unsigned* grid_out,
+                         bool launch) {
   const size_t smem = smem_bytes<K>(prm.max_rec_words);
   auto kern = phenotype_kernel<K, GAP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -628,6 +700,10 @@ int launch_shape(const hp::PhenParams& prm, cudaStream_t stream, unsigned grid_l
   unsigned long long grid = (unsigned long long)sms * per_sm;
   if (grid > prm.total_items) grid = prm.total_items;
   if (grid_limit && grid > grid_limit) grid = grid_limit;
+  if (grid < 1) grid = 1;
+  if (grid_out) *grid_out = (unsigned)grid;
+  if (!launch) return HP_OK;
+  if (!prm.wlist || prm.wl_ctas < grid) return hp::fail(HP_EINVAL, "phenotype kernel: work lists not set up for the grid");
   kern<<<(unsigned)grid, K::THREADS, smem, stream>>>(prm);
   e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "phenotype_kernel launch");
@@ -652,20 +728,49 @@ void default_tile_cfg(int* reg_bits, int* tile) {
   *tile = 256;
 }
 
-int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit) {
+namespace {
+int grid_or_launch(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit,
+                   unsigned* grid, bool launch) {
   // thresholds above 1 have one compiled shape (the default)
-  if (prm.gap2 > 2u) return launch_shape<Cfg<5, 256>, true>(prm, stream, grid_limit);
+  if (prm.gap2 > 2u) return shape_grid_or_launch<Cfg<5, 256>, true>(prm, stream, grid_limit, grid, launch);
   switch (reg_bits * 1000 + tile) {
-    case 4064: return launch_shape<Cfg<4, 64>>(prm, stream, grid_limit);
-    case 4128: return launch_shape<Cfg<4, 128>>(prm, stream, grid_limit);
-    case 5064: return launch_shape<Cfg<5, 64>>(prm, stream, grid_limit);
-    case 5128: return launch_shape<Cfg<5, 128>>(prm, stream, grid_limit);
-    case 5256: return launch_shape<Cfg<5, 256>>(prm, stream, grid_limit);
-    case 6064: return launch_shape<Cfg<6, 64>>(prm, stream, grid_limit);
-    case 6128: return launch_shape<Cfg<6, 128>>(prm, stream, grid_limit);
-    case 6256: return launch_shape<Cfg<6, 256>>(prm, stream, grid_limit);
+    case 4064: return shape_grid_or_launch<Cfg<4, 64>>(prm, stream, grid_limit, grid, launch);
+    case 4128: return shape_grid_or_launch<Cfg<4, 128>>(prm, stream, grid_limit, grid, launch);
+    case 5064: return shape_grid_or_launch<Cfg<5, 64>>(prm, stream, grid_limit, grid, launch);
+    case 5128: return shape_grid_or_launch<Cfg<5, 128>>(prm, stream, grid_limit, grid, launch);
+    case 5256: return shape_grid_or_launch<Cfg<5, 256>>(prm, stream, grid_limit, grid, launch);
+    case 6064: return shape_grid_or_launch<Cfg<6, 64>>(prm, stream, grid_limit, grid, launch);
+    case 6128: return shape_grid_or_launch<Cfg<6, 128>>(prm, stream, grid_limit, grid, launch);
+    case 6256: return shape_grid_or_launch<Cfg<6, 256>>(prm, stream, grid_limit, grid, launch);
     default: return fail(HP_EINVAL, "unsupported tile configuration");
   }
+}
+}  // namespace
+
+int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit) {
+  return grid_or_launch(prm, reg_bits, tile, stream, grid_limit, nullptr, true);
+}
+
+int launch_block_bytes(const PhenParams& prm, int reg_bits, int tile, unsigned grid_limit, size_t* bytes,
+                       unsigned* ctas) {
+  unsigned grid = 0;
+  const int rc = grid_or_launch(prm, reg_bits, tile, nullptr, grid_limit, &grid, false);
+  if (rc != HP_OK) return rc;
+  int max_tiles = 0;
+  for (int i = 0; i < prm.ninst; i++) max_tiles = std::max(max_tiles, prm.inst[i].ntiles);
+  const size_t stride = ((size_t)(1u << kRoles) + (size_t)max_tiles + 1 + 63) / 64 * 64;  // uint16, 128-byte rows
+  *ctas = grid;
+  *bytes = 256 + stride * 2 * grid;
+  return HP_OK;
+}
+
+void bind_launch_block(PhenParams& prm, void* block, unsigned ctas) {
+  int max_tiles = 0;
+  for (int i = 0; i < prm.ninst; i++) max_tiles = std::max(max_tiles, prm.inst[i].ntiles);
+  prm.ctrl = static_cast<unsigned*>(block);
+  prm.wlist = reinterpret_cast<uint16_t*>(static_cast<char*>(block) + 256);
+  prm.wl_stride = (unsigned)(((size_t)(1u << kRoles) + (size_t)max_tiles + 1 + 63) / 64 * 64);
+  prm.wl_ctas = ctas;
 }
 
 bool half_enumeration_enabled() {
@@ -717,6 +822,8 @@ int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const 
   prm.max_rec_words = 0;
   prm.one = 1u;
   prm.gap2 = 2u;
+  prm.spin = wait_limit(kSpinLimit);
+  prm.spin_handover = wait_limit(1ll << 22);
   unsigned long long items = 0;
   int nb = 0;
   for (int q = 0; q < n; q++) {
@@ -797,14 +904,22 @@ int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const u
     delete prm;
     return rc;
   }
-  unsigned* ctrl = nullptr;
-  cudaError_t e = cudaMallocAsync(&ctrl, kPhenCtrlBytes, st);
+  size_t bytes = 0;
+  unsigned ctas = 0;
+  rc = launch_block_bytes(*prm, reg_bits, tile, grid_limit, &bytes, &ctas);
+  if (rc != HP_OK) {
+    delete prm;
+    return rc;
+  }
+  void* block = nullptr;
+  cudaError_t e = cudaMallocAsync(&block, bytes, st);
   if (e != cudaSuccess) {
     delete prm;
-    return cuda_fail(e, "cudaMallocAsync(phenotype control words)");
+    return cuda_fail(e, "cudaMallocAsync(phenotype control words and work lists)");
   }
+  unsigned* ctrl = static_cast<unsigned*>(block);
   cudaMemsetAsync(ctrl, 0, kPhenCtrlBytes, st);
-  prm->ctrl = ctrl;
+  bind_launch_block(*prm, block, ctas);
   rc = launch_phenotype(*prm, reg_bits, tile, st, grid_limit);
   delete prm;
   unsigned herr = 0;
@@ -814,7 +929,11 @@ int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const u
     if (e != cudaSuccess) rc = cuda_fail(e, "phenotype kernel execution");
   }
   cudaFreeAsync(ctrl, st);
-  if (rc == HP_OK && (herr & kErrTimeout)) rc = fail(HP_ETIMEOUT, "phenotype kernel: a bulk-copy wait timed out");
+  if (rc == HP_OK && (herr & kErrDrain))
+    rc = fail(HP_ETIMEOUT, "phenotype kernel: a wait timed out and bulk copies were still in flight at exit; "
+                           "the output is invalid");
+  else if (rc == HP_OK && (herr & kErrTimeout))
+    rc = fail(HP_ETIMEOUT, "phenotype kernel: a bounded wait timed out; the output is invalid");
   return rc;
 }
 

@@ -44,6 +44,11 @@ struct PhenParams {
   PhenInst inst[kPhenMaxInst];
   PhenBlock blocks[kPhenMaxBlocks];
   uint32_t gap2;       // 2 x the energy-gap threshold (2: strict uniqueness, the paper's threshold 1)
+  long long spin;           // polls of a bulk-copy wait before it gives up (hp_set_wait_limit)
+  long long spin_handover;  // polls of a coefficient-buffer hand-over wait before it gives up
+  // pass-2 work lists: wl_ctas lists of wl_stride uint16 each (2^14 entries + max ntiles + 1 offsets)
+  uint16_t* wlist;
+  unsigned wl_stride, wl_ctas;
 };
 
 bool tile_cfg_supported(int reg_bits, int tile);
@@ -51,6 +56,12 @@ void default_tile_cfg(int* reg_bits, int* tile);
 int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
                    int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm);
 int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit);
+// Device block a launch needs (control words, then one pass-2 work list per CTA): its size and the
+// number of CTAs the launch will use; bind_launch_block points prm.ctrl / prm.wlist into it.  The
+// first kPhenCtrlBytes must be zeroed before each launch.
+int launch_block_bytes(const PhenParams& prm, int reg_bits, int tile, unsigned grid_limit, size_t* bytes,
+                       unsigned* ctas);
+void bind_launch_block(PhenParams& prm, void* block, unsigned ctas);
 // plan + per-call control words + launch + error read-back (synchronises the stream); a
 // gap_threshold above 1 runs the one shape compiled for it (reg_bits 5, tile 256)
 int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,

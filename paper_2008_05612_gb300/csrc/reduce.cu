@@ -2,6 +2,7 @@
 // designability, the Eq. 2 numerators behind robustness and phi_del, and the
 // neutral networks (connected components of same-phenotype single flips).
 // All three are HBM-bound passes over the int32 map.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,12 +61,34 @@ __global__ void __launch_bounds__(kHistThreads) hist_partial(const int32_t* __re
   for (int b = threadIdx.x; b <= S; b += blockDim.x) row[b] = bins[b];
 }
 
-__global__ void hist_sum(const unsigned* __restrict__ partial, int rows, int S, unsigned long long* __restrict__ hist) {
+// hist[b] = (accumulate ? hist[b] : 0) + the column sum of the partial rows
+__global__ void hist_sum(const unsigned* __restrict__ partial, int rows, int S, unsigned long long* __restrict__ hist,
+                         int accumulate) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b > S) return;
-  unsigned long long s = 0;
+  unsigned long long s = accumulate ? hist[b] : 0ull;
   for (int r = 0; r < rows; r++) s += partial[(size_t)r * (S + 1) + b];
   hist[b] = s;
+}
+
+// Ids one partial row may count before its uint32 bins could wrap (a row counts about
+// count / rows ids, most of them into one bin): ranges beyond rows x this are split into passes.
+constexpr unsigned long long kHistIdsPerRow = 1ull << 31;
+
+// hist_partial + hist_sum over [0, count) in passes of at most rows x kHistIdsPerRow ids (a
+// multiple of 4, so every pass keeps the 16-byte alignment of d_phen), the later passes adding to
+// d_hist.
+cudaError_t launch_hist(const int32_t* d_phen, unsigned long long count, int S, unsigned* partial, int rows,
+                        unsigned* err, uint64_t* d_hist, size_t bins_bytes, cudaStream_t st) {
+  const int vec4 = ((uintptr_t)d_phen % 16) == 0;
+  const unsigned long long pass = (unsigned long long)rows * kHistIdsPerRow;
+  for (unsigned long long off = 0; off < count; off += pass) {
+    const unsigned long long n = std::min(pass, count - off);
+    hist_partial<<<rows, kHistThreads, bins_bytes, st>>>(d_phen + off, n, S, partial, err, vec4);
+    hist_sum<<<(S + 1 + 255) / 256, 256, 0, st>>>(partial, rows, S, reinterpret_cast<unsigned long long*>(d_hist),
+                                                 off > 0);
+  }
+  return cudaGetLastError();
 }
 
 // fallback for phenotype counts too large for one shared-memory histogram
@@ -269,12 +292,7 @@ extern "C" int hp_designability(const int32_t* d_phen, uint64_t count, int32_t S
     if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_designability: cudaMallocAsync(partials)");
     if (rc == HP_OK) {
       e = cudaFuncSetAttribute(hist_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bins_bytes);
-      const int vec4 = ((uintptr_t)d_phen % 16) == 0;
-      if (e == cudaSuccess) {
-        hist_partial<<<rows, kHistThreads, bins_bytes, st>>>(d_phen, count, S, partial, err, vec4);
-        hist_sum<<<(S + 1 + 255) / 256, 256, 0, st>>>(partial, rows, S, reinterpret_cast<unsigned long long*>(d_hist));
-        e = cudaGetLastError();
-      }
+      if (e == cudaSuccess) e = launch_hist(d_phen, count, S, partial, rows, err, d_hist, bins_bytes, st);
       if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_designability: launch");
       cudaFreeAsync(partial, st);
     }
@@ -302,22 +320,27 @@ extern "C" int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64
   cudaMemsetAsync(err, 0, 16, st);
   cudaMemsetAsync(d_neutral, 0, sizeof(uint64_t) * (size_t)(S + 1), st);
   cudaMemsetAsync(d_to_del, 0, sizeof(uint64_t) * (size_t)(S + 1), st);
+  e = hp::launch_robustness(d_phen, N, S, reinterpret_cast<unsigned long long*>(d_neutral),
+                            reinterpret_cast<unsigned long long*>(d_to_del), negcount, err, st);
+  const int rc = e == cudaSuccess ? HP_OK : hp::cuda_fail(e, "hp_robustness: launch");
+  return finish_with_err(err, st, "hp_robustness", rc);
+}
+
+namespace hp {
+
+cudaError_t launch_robustness(const int32_t* d_phen, int N, int S, unsigned long long* neutral,
+                              unsigned long long* to_del, unsigned long long* negcount, unsigned* err, cudaStream_t st) {
   const int k = std::min((int)N, kRobTileBits);
   const unsigned long long tiles = 1ull << (N - k);
   const size_t smem = sizeof(int32_t) << k;
-  int rc = HP_OK;
-  e = cudaFuncSetAttribute(robustness_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) {
-    robustness_tiles<<<(unsigned)tiles, kRobThreads, smem, st>>>(
-        d_phen, N, S, reinterpret_cast<unsigned long long*>(d_neutral), reinterpret_cast<unsigned long long*>(d_to_del),
-        negcount, err);
-    robustness_finish<<<1, 1024, 0, st>>>(N, S, reinterpret_cast<unsigned long long*>(d_neutral),
-                                          reinterpret_cast<unsigned long long*>(d_to_del), negcount);
-    e = cudaGetLastError();
-  }
-  if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_robustness: launch");
-  return finish_with_err(err, st, "hp_robustness", rc);
+  cudaError_t e = cudaFuncSetAttribute(robustness_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  robustness_tiles<<<(unsigned)tiles, kRobThreads, smem, st>>>(d_phen, N, S, neutral, to_del, negcount, err);
+  robustness_finish<<<1, 1024, 0, st>>>(N, S, neutral, to_del, negcount);
+  return cudaGetLastError();
 }
+
+}  // namespace hp
 
 extern "C" int hp_neutral_components(const int32_t* d_phen, int32_t N, int32_t S, int32_t* d_label, uint64_t* d_ncomp,
                                      void* stream) {
@@ -361,19 +384,53 @@ static __device__ __align__(256) unsigned g_noalloc_scratch[kNoAllocWords];
 
 std::mutex g_noalloc_mu;
 unsigned* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {0};  // id of the context the address belongs to
 
-// Device address of the scratch array on the current device (set up on first use).
+// Unique id of the current CUDA context (0 if the driver cannot tell).  A device reset destroys
+// the context and the module with its array; the next context gets a new id, so an address
+// looked up in the old context is never reused.  The driver calls are reached through the
+// runtime's entry-point query, so the library does not link libcuda itself.
+unsigned long long current_context_id() {
+  typedef CUresult (*get_current_fn)(CUcontext*);
+  typedef CUresult (*get_id_fn)(CUcontext, unsigned long long*);
+  static get_current_fn get_current = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? reinterpret_cast<get_current_fn>(f)
+               : nullptr;
+  }();
+  static get_id_fn get_id = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? reinterpret_cast<get_id_fn>(f)
+               : nullptr;
+  }();
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context: looked up (cudaGetSymbolAddress)
+// on the first call in each context of each device, then cached under the context's id.
 int noalloc_scratch(unsigned** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kNoAllocMaxDevices) return hp::fail(HP_EUNSUPPORTED, "hp_designability_noalloc: device index too large");
+  // 0 (no context bound to this thread yet, or no answer from the driver) always looks the address up
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || ctx == 0 || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: cudaGetSymbolAddress");
     g_noalloc_ptr[dev] = static_cast<unsigned*>(p);
+    g_noalloc_ctx[dev] = ctx;
   }
   *out = g_noalloc_ptr[dev];
   return HP_OK;
@@ -412,12 +469,7 @@ extern "C" int hp_designability_noalloc(const int32_t* d_phen, uint64_t count, i
     e = cudaMemsetAsync(d_hist, 0, sizeof(uint64_t) * bins, st);
   } else {
     e = cudaFuncSetAttribute(hist_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bins_bytes);
-    if (e == cudaSuccess) {
-      const int vec4 = ((uintptr_t)d_phen % 16) == 0;
-      hist_partial<<<rows, kHistThreads, bins_bytes, st>>>(d_phen, count, S, partial, err, vec4);
-      hist_sum<<<(unsigned)((bins + 255) / 256), 256, 0, st>>>(partial, rows, S, reinterpret_cast<unsigned long long*>(d_hist));
-      e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = launch_hist(d_phen, count, S, partial, rows, err, d_hist, bins_bytes, st);
   }
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_designability_noalloc: launch");
   unsigned herr = 0;

@@ -57,6 +57,7 @@ struct Params {
   int M, N, K, mt, nt, nr, units, ksplit;
   TcEpilogue ep;
   unsigned* err;
+  uint32_t spin;  // polls of a pipeline wait before it gives up (the exit drains keep SPIN_LIMIT)
 };
 
 struct Unit {
@@ -87,20 +88,19 @@ __device__ __forceinline__ bool poll(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase of `bar` with this parity.  False if another role aborted or, after
-// SPIN_LIMIT polls, this one gives up (then it raises the abort flag and the error word).
-__device__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag, unsigned* err) {
+// Wait for the phase of `bar` with this parity.  False if another role aborted (checked every
+// 256 polls) or, after `limit` polls, this one gives up (then it raises the abort flag and the
+// error word); a limit of 0 gives up before the first poll.
+__device__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag, unsigned* err, uint32_t limit) {
   const uint32_t b = sa(bar);
   for (uint32_t i = 0;; i++) {
-    if (poll(b, parity)) return true;
-    if ((i & 255) == 255) {
-      if (*abort_flag) return false;
-      if (i >= SPIN_LIMIT) {
-        *abort_flag = 1;
-        if (err) atomicOr(err, 1u);
-        return false;
-      }
+    if (i >= limit) {
+      *abort_flag = 1;
+      if (err) atomicOr(err, 1u);
+      return false;
     }
+    if (poll(b, parity)) return true;
+    if ((i & 255) == 255 && *abort_flag) return false;
   }
 }
 
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         for (int kc = w.kb; kc < w.ke; kc++, it++) {
           const uint32_t s = it % STAGES, r = it / STAGES;
           // round r reuses the stage after the MMAs of round r - 1 committed (round 0: fresh barrier)
-          if (!wait_or_abort(&empty[s], (r & 1) ^ 1, abort_flag, err)) {
+          if (!wait_or_abort(&empty[s], (r & 1) ^ 1, abort_flag, err, p.spin)) {
             ok = false;
             break;
           }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
       const Unit w = unit_of(p, u);
       for (int tn = w.nb; tn < w.ne && ok; tn++, tl++) {
         const uint32_t a = tl & 1, ar = tl >> 1;
-        if (!wait_or_abort(&tmem_empty[a], (ar & 1) ^ 1, abort_flag, err)) {
+        if (!wait_or_abort(&tmem_empty[a], (ar & 1) ^ 1, abort_flag, err, p.spin)) {
           ok = false;
           break;
         }
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         const uint32_t acc_addr = tmem + a * TN;
         for (int kc = w.kb; kc < w.ke; kc++, it++) {
           const uint32_t s = it % STAGES, r = it / STAGES;
-          if (!wait_or_abort(&full[s], r & 1, abort_flag, err)) {
+          if (!wait_or_abort(&full[s], r & 1, abort_flag, err, p.spin)) {
             ok = false;
             break;
           }
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
       }
       for (int tn = w.nb; tn < w.ne; tn++, tl++) {
         const uint32_t a = tl & 1, ar = tl >> 1;
-        if (!wait_or_abort(&tmem_full[a], ar & 1, abort_flag, err)) {
+        if (!wait_or_abort(&tmem_full[a], ar & 1, abort_flag, err, p.spin)) {
           ok = false;
           break;
         }
@@ -648,7 +648,8 @@ int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
   const int nk = (K + TK - 1) / TK;
   if (ep.ksplit < 1 || ep.ksplit > nk || (ep.ksplit > 1 && (ep.kt || ep.Cb || ep.bias || ep.relu || !ep.Cf)))
     return fail(HP_EINVAL, "tc_gemm: split-K needs store mode with an fp32 output only and at most one slice per K chunk");
-  Params p{M, N, K, (M + TM - 1) / TM, (N + TN - 1) / TN, 0, 0, ep.ksplit, ep, err};
+  Params p{M, N, K, (M + TM - 1) / TM, (N + TN - 1) / TN, 0, 0, ep.ksplit, ep, err,
+           (uint32_t)std::min<long long>(wait_limit(SPIN_LIMIT), 0xFFFFFFFFll)};
   p.nr = (ep.kt > 0 || ep.kt == -1) ? tc_topk_lists(M, N) / kTcListsPerTile : p.nt;
   p.units = p.mt * p.nr * p.ksplit;
   switch (ep.kt) {
