@@ -344,6 +344,23 @@ int hp_stream_shards(const hp_structs* s, int32_t shard_bits, int32_t window, co
 int hp_neutral_components(const int32_t* d_phen, int32_t N, int32_t S, int32_t* d_label, uint64_t* d_ncomp,
                           void* stream);
 
+/* Neutral-network counts of a space too large for one label array (the 6x6
+ * space of 2^36 genotypes, Sections 3.1 and 4; networks as in
+ * hp_neutral_components, Section 1): h_ncomp[p] = number of connected
+ * components of phenotype p over the whole space [0, 2^N), equal to
+ * hp_neutral_components' d_ncomp of the full map where that fits.  The space
+ * is cut into 2^shard_bits shards of 2^(N - shard_bits) <= 2^31 ids; each
+ * shard's local components come from the union-find of
+ * hp_neutral_components over the shard, the flips of the shard bits join them
+ * (distinct joins collected per pair of neighbouring shards on the device),
+ * and a host union-find merges them.  window: resident shard maps,
+ * >= 2^(shard_bits-1) + 1 (HP_EINVAL before any device work otherwise).
+ *   h_ncomp: host uint64[S]; *h_maps_computed (may be NULL): shard maps made.
+ * Allocates device memory for the window, two label buffers and the join
+ * tables; synchronises `stream`. */
+int hp_stream_components(const hp_structs* s, int32_t shard_bits, int32_t window, uint64_t* h_ncomp,
+                         int32_t* h_maps_computed, void* stream);
+
 /* Thread-local text of the last failure in this library (never NULL). */
 const char* hp_last_error(void);
 

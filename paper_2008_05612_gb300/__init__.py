@@ -26,7 +26,7 @@ EXPORTS = (
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
     "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
     "hp_batch_plan_free", "hp_sequence_scan", "hp_sequence_scan_gap", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
-    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_phi_matrix", "hp_robustness_cross", "hp_stream_shards",
+    "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_phi_matrix", "hp_robustness_cross", "hp_stream_shards", "hp_stream_components",
     "hp_neutral_components",
     "hp_last_error", "hp_set_wait_limit",
 )
@@ -94,6 +94,7 @@ def lib():
         L.hp_phi_matrix.argtypes = [vp, i32, i32, u64, vp, vp, vp, vp, vp]
         L.hp_robustness_cross.argtypes = [vp, vp, u64, i32, vp, vp, vp]
         L.hp_stream_shards.argtypes = [vp, i32, i32, ctypes.c_char_p, vp, vp, vp, vp, vp]
+        L.hp_stream_components.argtypes = [vp, i32, i32, vp, vp, vp]
         L.hp_last_error.restype = ctypes.c_char_p
         L.hp_set_wait_limit.argtypes = [ctypes.c_int64]
         for name in EXPORTS:
@@ -474,6 +475,17 @@ def stream_shards(structs: Structs, shard_bits: int, window: int | None = None, 
                                   to_del.ctypes.data_as(ctypes.c_void_p), ctypes.byref(computed),
                                   _stream_ptr(stream) if _cuda_ready() else None))
     return hist, neutral, to_del, computed.value
+
+
+def stream_components(structs: Structs, shard_bits: int, window: int | None = None, stream=None):
+    """hp_stream_components: (ncomp numpy uint64[S], shard maps computed) over the whole space."""
+    ncomp = np.zeros(structs.S, dtype=np.uint64)
+    computed = ctypes.c_int32(0)
+    if window is None:
+        window = (1 << (shard_bits - 1)) + 1 if shard_bits > 0 else 1
+    _check(lib().hp_stream_components(structs.handle, shard_bits, window, ncomp.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(computed), _stream_ptr(stream) if _cuda_ready() else None))
+    return ncomp, computed.value
 
 
 def _cuda_ready():

@@ -52,14 +52,30 @@ struct Record {
   bool have = false;
 };
 
+// FNV-1a (64-bit) of a record's counters, stored in its header: a record whose payload does not
+// match (a flipped bit, a torn or foreign file) is not reused, so its shard is computed again.
+uint64_t payload_sum(const std::vector<uint64_t>& v) {
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* c = reinterpret_cast<const unsigned char*>(v.data());
+  for (size_t i = 0; i < v.size() * sizeof(uint64_t); i++) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// header: table hash, payload words, payload checksum
 bool read_record(const std::string& path, uint64_t hash, size_t words, Record& r) {
   FILE* f = fopen(path.c_str(), "rb");
   if (!f) return false;
-  uint64_t hdr[2] = {0, 0};
+  uint64_t hdr[3] = {0, 0, 0};
   r.v.assign(words, 0);
-  bool ok = fread(hdr, 8, 2, f) == 2 && hdr[0] == hash && hdr[1] == words && fread(r.v.data(), 8, words, f) == words;
+  bool ok = fread(hdr, 8, 3, f) == 3 && hdr[0] == hash && hdr[1] == words && fread(r.v.data(), 8, words, f) == words;
+  unsigned char extra;
+  ok = ok && fread(&extra, 1, 1, f) == 0 && payload_sum(r.v) == hdr[2];
   fclose(f);
   r.have = ok;
+  if (!ok) r.v.clear();
   return ok;
 }
 
@@ -67,8 +83,8 @@ bool write_record(const std::string& path, uint64_t hash, const std::vector<uint
   const std::string tmp = path + ".tmp";
   FILE* f = fopen(tmp.c_str(), "wb");
   if (!f) return false;
-  const uint64_t hdr[2] = {hash, (uint64_t)v.size()};
-  bool ok = fwrite(hdr, 8, 2, f) == 2 && fwrite(v.data(), 8, v.size(), f) == v.size();
+  const uint64_t hdr[3] = {hash, (uint64_t)v.size(), payload_sum(v)};
+  bool ok = fwrite(hdr, 8, 3, f) == 3 && fwrite(v.data(), 8, v.size(), f) == v.size();
   ok = (fclose(f) == 0) && ok;
   return ok && rename(tmp.c_str(), path.c_str()) == 0;
 }
