@@ -30,7 +30,7 @@ DIMS = (3, 3, 3)
 WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformations (51,704 classes)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full 3x3x3 phenotype-kernel launch, from
 # an ncu capture of the current kernel; None whenever the kernel has changed since the last capture.
-TRAFFIC_PER_LAUNCH = 1_767_912_704
+TRAFFIC_PER_LAUNCH = None
 
 
 def dist_env():
@@ -302,6 +302,43 @@ def map_block_6x6(hp, torch, peak_ops: float, bits: int = 27, reps: int = 3):
                          "note": "0.5 packed max per performed evaluation (all 2^27 ids of the block are evaluated)"}}
 
 
+BATCH_BOXES = ((4, 4), (4, 5), (5, 5), (2, 3, 4), (3, 3, 3))
+
+
+def small_boxes_and_batch(hp, torch, reps: int = 3):
+    """Whole maps of the other boxes of the batched workload, one launch each (CUDA events, 1 warm-up +
+    `reps` launches), and the same five maps in ONE persistent batched launch."""
+    stream = torch.cuda.current_stream()
+    libs = [hp.Structs(d) for d in BATCH_BOXES]
+    outs = [torch.empty(1 << s.N, dtype=torch.int32, device="cuda") for s in libs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    singles = {}
+    for d, s, o in zip(BATCH_BOXES, libs, outs):
+        ms = timed(lambda: hp.phenotype_map(s, 0, 1 << s.N, out=o))
+        n = 1 << s.N
+        performed = performed_sequences(s.N) * s.S_dir
+        singles["x".join(map(str, d))] = {"sequences": n, "conformations": s.S_dir, "map_ms": ms,
+                                          "evals_per_s": n * s.S_dir / (ms * 1e-3),
+                                          "performed_evals_per_s": performed / (ms * 1e-3)}
+    ranges = [(0, 1 << s.N) for s in libs]
+    ms_batch = timed(lambda: hp.phenotype_map_batch(libs, ranges, outs))
+    total = sum((1 << s.N) * s.S_dir for s in libs)
+    return {"singles": singles, "batch": {"boxes": ["x".join(map(str, d)) for d in BATCH_BOXES], "map_ms": ms_batch,
+                                          "sum_of_singles_ms": sum(v["map_ms"] for v in singles.values()),
+                                          "evals_per_s": total / (ms_batch * 1e-3)}}
+
+
 PROPOSAL_ROWS = 16384  # ids per proposal chunk (the network's max_batch)
 
 
@@ -483,6 +520,8 @@ def main():
                     help="time the proposal network's training step alone (batch 4096, 3x3x3 classes)")
     ap.add_argument("--proposal-case", action="store_true",
                     help="profiling case: top-4 proposals of an untrained 3x3x3 network for 65,536 ids, W + K times")
+    ap.add_argument("--small-boxes", action="store_true",
+                    help="only the whole maps of 4x4, 4x5, 5x5, 2x3x4, 3x3x3 one by one and in one batched launch")
     ap.add_argument("--map-only", default=None, metavar="BOX:BITS",
                     help="profiling case: only the phenotype map of ids [0, 2^BITS) of BOX (e.g. 6x6:27)")
     args = ap.parse_args()
@@ -490,6 +529,16 @@ def main():
         return run_reference(args)
     if args.map_only:
         return run_map_only(args)
+    if args.small_boxes:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        import paper_2008_05612_gb300 as hp
+
+        print(json.dumps(small_boxes_and_batch(hp, torch)))
+        return 0
     if args.stream:
         return run_stream(args)
 
@@ -677,6 +726,7 @@ def main():
     }
     if rank == 0:
         line["box_6x6"] = map_block_6x6(hp, torch, peak_ops)
+        line["other_boxes"] = small_boxes_and_batch(hp, torch)
     if rank == 0 and not args.no_learned:
         line["learned"] = {}
         for name, fn in (("3x3x3", lambda: learned_leg(hp, s, torch)), ("6x6", lambda: learned_leg_6x6(hp, torch))):

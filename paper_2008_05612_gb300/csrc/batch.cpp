@@ -44,7 +44,7 @@ int shape_of(const hp_tile_cfg* cfg, const hp_structs* first, int* r, int* t) {
 struct hp_batch_plan {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
-  unsigned* ctrl = nullptr;
+  std::vector<unsigned*> ctrl;  // one control block per captured launch (role class)
   int device = -1;
 };
 
@@ -89,7 +89,9 @@ extern "C" int hp_phenotype_map_batch(const hp_structs* const* libs, const uint6
   int r = 0, t = 0;
   int rc = shape_of(cfg, libs[0], &r, &t);
   if (rc != HP_OK) return rc;
-  return hp::run_phenotype(libs, begins, counts, n, d_phen, nullptr, r, t, (cudaStream_t)stream, 0);
+  // no shape given: the role count follows the blocks (all boxes of the launch share it)
+  const bool auto_roles = !cfg && !libs[0]->tile_reg_bits;
+  return hp::run_phenotype(libs, begins, counts, n, d_phen, nullptr, r, t, (cudaStream_t)stream, 0, 1, auto_roles);
 }
 
 extern "C" int hp_autotune(hp_structs* s, hp_tile_cfg* best, float* ms, void* stream) {
@@ -187,32 +189,56 @@ extern "C" int hp_batch_plan_create(const hp_structs* const* libs, const uint64_
   int r = 0, t = 0;
   int rc = shape_of(cfg, libs[0], &r, &t);
   if (rc != HP_OK) return rc;
-  hp::PhenParams* prm = new (std::nothrow) hp::PhenParams();
   hp_batch_plan* plan = new (std::nothrow) hp_batch_plan();
-  if (!prm || !plan) {
-    delete prm;
-    delete plan;
-    return hp::fail(HP_ENOMEM, "hp_batch_plan_create: out of host memory");
-  }
-  // tables are uploaded here, before capture begins
-  rc = hp::plan_phenotype(libs, begins, counts, n, d_phen, nullptr, t, *prm);
-  cudaError_t e = cudaSuccess;
-  if (rc == HP_OK && prm->total_items) {
-    cudaGetDevice(&plan->device);
-    size_t bytes = 0;
-    unsigned ctas = 0;
-    rc = hp::launch_block_bytes(*prm, r, t, 0, &bytes, &ctas);
-    if (rc == HP_OK) {
-      e = cudaMalloc(&plan->ctrl, bytes);
-      if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaMalloc");
-      else hp::bind_launch_block(*prm, plan->ctrl, ctas);
+  if (!plan) return hp::fail(HP_ENOMEM, "hp_batch_plan_create: out of host memory");
+  cudaGetDevice(&plan->device);
+  // no shape given: boxes are grouped by role count, one persistent launch per group (all in the graph)
+  std::vector<int> cls(n, 14);
+  const bool auto_roles = !cfg && !libs[0]->tile_reg_bits;
+  if (auto_roles) rc = hp::role_classes(libs, begins, counts, n, d_phen, t, cls);
+  // plans (tables are uploaded here, before capture begins) and their device blocks
+  std::vector<hp::PhenParams*> prms;
+  std::vector<int> shape_r, shape_t;
+  for (const int c : {14, 13, 12, 11}) {
+    if (rc != HP_OK) break;
+    std::vector<const hp_structs*> l;
+    std::vector<uint64_t> bg, ct;
+    std::vector<int32_t*> o;
+    for (int i = 0; i < n; i++)
+      if (cls[i] == c) {
+        l.push_back(libs[i]);
+        bg.push_back(begins[i]);
+        ct.push_back(counts[i]);
+        o.push_back(d_phen[i]);
+      }
+    if (l.empty()) continue;
+    int r2 = r, t2 = t, roles = 14;
+    if (c != 14) hp::small_roles_shape(c, &roles, &r2, &t2);
+    hp::PhenParams* prm = new (std::nothrow) hp::PhenParams();
+    if (!prm) {
+      rc = hp::fail(HP_ENOMEM, "hp_batch_plan_create: out of host memory");
+      break;
     }
-  } else if (rc == HP_OK) {
-    cudaGetDevice(&plan->device);
-    e = cudaMalloc(&plan->ctrl, hp::kPhenCtrlBytes);
-    if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaMalloc");
+    prms.push_back(prm);
+    shape_r.push_back(r2);
+    shape_t.push_back(t2);
+    rc = hp::plan_phenotype(l.data(), bg.data(), ct.data(), (int)l.size(), o.data(), nullptr, t2, *prm, c);
+    if (rc != HP_OK) break;
+    size_t bytes = hp::kPhenCtrlBytes;
+    unsigned ctas = 0;
+    if (prm->total_items) rc = hp::launch_block_bytes(*prm, r2, t2, 0, &bytes, &ctas);
+    if (rc != HP_OK) break;
+    unsigned* block = nullptr;
+    cudaError_t e = cudaMalloc(&block, bytes);
+    if (e != cudaSuccess) {
+      rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaMalloc");
+      break;
+    }
+    plan->ctrl.push_back(block);
+    if (prm->total_items) hp::bind_launch_block(*prm, block, ctas);
   }
   cudaStream_t cap = nullptr;
+  cudaError_t e = cudaSuccess;
   if (rc == HP_OK) {
     e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaStreamCreate");
@@ -220,8 +246,11 @@ extern "C" int hp_batch_plan_create(const hp_structs* const* libs, const uint64_
   if (rc == HP_OK) {
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaMemsetAsync(plan->ctrl, 0, hp::kPhenCtrlBytes, cap);
-      int lrc = prm->total_items ? hp::launch_phenotype(*prm, r, t, cap, 0) : HP_OK;
+      int lrc = HP_OK;
+      for (size_t q = 0; q < prms.size() && lrc == HP_OK; q++) {
+        cudaMemsetAsync(plan->ctrl[q], 0, hp::kPhenCtrlBytes, cap);
+        if (prms[q]->total_items) lrc = hp::launch_phenotype(*prms[q], shape_r[q], shape_t[q], cap, 0);
+      }
       cudaError_t e2 = cudaStreamEndCapture(cap, &plan->graph);
       if (lrc != HP_OK) rc = lrc;
       else if (e2 != cudaSuccess) rc = hp::cuda_fail(e2, "hp_batch_plan_create: cudaStreamEndCapture");
@@ -234,7 +263,7 @@ extern "C" int hp_batch_plan_create(const hp_structs* const* libs, const uint64_
     if (e != cudaSuccess) rc = hp::cuda_fail(e, "hp_batch_plan_create: cudaGraphInstantiate");
   }
   if (cap) cudaStreamDestroy(cap);
-  delete prm;
+  for (hp::PhenParams* prm : prms) delete prm;
   (void)stream;
   if (rc != HP_OK) {
     hp_batch_plan_free(plan);
@@ -252,12 +281,15 @@ extern "C" int hp_batch_plan_launch(hp_batch_plan* plan, void* stream) {
 }
 
 extern "C" int hp_batch_plan_status(hp_batch_plan* plan, void* stream) {
-  if (!plan || !plan->ctrl) return hp::fail(HP_EINVAL, "hp_batch_plan_status: invalid plan");
-  unsigned herr = 0;
-  cudaError_t e = cudaMemcpyAsync(&herr, plan->ctrl, sizeof(unsigned), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (!plan || plan->ctrl.empty()) return hp::fail(HP_EINVAL, "hp_batch_plan_status: invalid plan");
+  std::vector<unsigned> herr(plan->ctrl.size(), 0u);
+  cudaError_t e = cudaSuccess;
+  for (size_t q = 0; q < plan->ctrl.size() && e == cudaSuccess; q++)
+    e = cudaMemcpyAsync(&herr[q], plan->ctrl[q], sizeof(unsigned), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_batch_plan_status");
-  if (herr) return hp::fail(HP_ETIMEOUT, "hp_batch_plan_status: a bulk-copy wait timed out");
+  for (unsigned h : herr)
+    if (h) return hp::fail(HP_ETIMEOUT, "hp_batch_plan_status: a bounded device wait timed out");
   return HP_OK;
 }
 
@@ -268,7 +300,7 @@ extern "C" void hp_batch_plan_free(hp_batch_plan* plan) {
   if (plan->device >= 0) cudaSetDevice(plan->device);
   if (plan->exec) cudaGraphExecDestroy(plan->exec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
-  if (plan->ctrl) cudaFree(plan->ctrl);
+  for (unsigned* c : plan->ctrl) cudaFree(c);
   if (cur >= 0 && plan->device >= 0) cudaSetDevice(cur);
   delete plan;
 }

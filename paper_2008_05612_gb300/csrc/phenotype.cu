@@ -127,10 +127,11 @@ __device__ __forceinline__ uint32_t odd_part(const uint32_t* r, int NE, uint32_t
 }
 
 // Compile-time shape: R register bits (2^(R-1) packed registers of two
-// sequences per thread), T conformations per shared-memory tile, 2^(9-R) warps.
-template <int R_, int T_>
+// sequences per thread), T conformations per shared-memory tile, ROLES even-pattern bits per CTA
+// (14, or fewer for boxes and ranges with fewer free even residues), 2^(ROLES-5-R) warps.
+template <int R_, int T_, int ROLES_ = kRoles>
 struct Cfg {
-  static constexpr int R = R_, T = T_, WB = kRoles - kLaneRoles - R_;
+  static constexpr int R = R_, T = T_, ROLES = ROLES_, WB = ROLES_ - kLaneRoles - R_;
   static constexpr int P = 1 << (R - 1);
   static constexpr int NW = 1 << WB;
   static constexpr int THREADS = 32 * NW;
@@ -174,9 +175,9 @@ __device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* e
       uint32_t* c = cbuf + tid * STRIDE;
       const int s = t * T + tid;
       if (s < in.S_dir) {
-        uint32_t a[kRoles];
+        uint32_t a[K::ROLES];
 #pragma unroll
-        for (int k = 0; k < kRoles; k++) a[k] = k < nroles ? 2u * coef(r[k], o) : 0u;
+        for (int k = 0; k < K::ROLES; k++) a[k] = k < nroles ? 2u * coef(r[k], o) : 0u;
         uint32_t extra = 0;
         for (int k = nroles; k < in.NE; k++)
           if ((ehigh >> k) & 1u) extra += coef(r[k], o);
@@ -357,29 +358,46 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         issued[b]++;
       }
       const uint32_t* cbuf = coefbuf + b * T * CSTRIDE;
+      // subset sums over the tree roles of one conformation (IMAD: x * one + a keeps them on the FMA
+      // pipe); the leaves (top tree bit set) are left to the fused add + max
+      auto tree = [&](const uint32_t* cs, uint32_t (&x)[P / 2], uint32_t (&tpv)[K::TP_WORDS]) {
+#pragma unroll
+        for (int j = 0; j < K::TP_WORDS; j += 4) {
+          const uint4 q = *reinterpret_cast<const uint4*>(cs + K::TP_OFF + j);
+          tpv[j] = q.x; tpv[j + 1] = q.y; tpv[j + 2] = q.z; tpv[j + 3] = q.w;
+        }
+        x[0] = cs[lane] * p.one + cs[K::WT_OFF + warp];
+#pragma unroll
+        for (int v = 1; v < P / 2; v++) {
+          const int hb = 31 - __clz(v);
+          x[v] = x[v ^ (1 << hb)] * p.one + tpv[hb];
+        }
+      };
       auto consume = [&](int s0, int s1) {
+        if constexpr (P <= 16) {
+          // two conformations at a time: the lower half of the registers takes both with one
+          // three-input packed max, the upper half with two fused add + max
+#pragma unroll 4
+          for (int s = s0; s < s1; s += 2) {
+            uint32_t x[P / 2], y[P / 2], tx[K::TP_WORDS], ty[K::TP_WORDS];
+            tree(cbuf + s * CSTRIDE, x, tx);
+            tree(cbuf + (s + 1) * CSTRIDE, y, ty);
+#pragma unroll
+            for (int v = 0; v < P / 2; v++) {
+              tmax[v] = __vimax3_u16x2(tmax[v], x[v], y[v]);
+              tmax[v + P / 2] = __viaddmax_u16x2(y[v], ty[R - 2], __viaddmax_u16x2(x[v], tx[R - 2], tmax[v + P / 2]));
+            }
+          }
+        } else {
 #pragma unroll 8
-        for (int s = s0; s < s1; s++) {
-          const uint32_t* cs = cbuf + s * CSTRIDE;
-          uint32_t tpv[K::TP_WORDS];
+          for (int s = s0; s < s1; s++) {
+            uint32_t x[P / 2], tx[K::TP_WORDS];
+            tree(cbuf + s * CSTRIDE, x, tx);
 #pragma unroll
-          for (int j = 0; j < K::TP_WORDS; j += 4) {
-            const uint4 q = *reinterpret_cast<const uint4*>(cs + K::TP_OFF + j);
-            tpv[j] = q.x; tpv[j + 1] = q.y; tpv[j + 2] = q.z; tpv[j + 3] = q.w;
-          }
-          // subset sums over the tree roles (IMAD: x * one + a keeps them on the FMA pipe); the
-          // leaves (top tree bit set) use the fused add + max
-          uint32_t x[P / 2];
-          x[0] = cs[lane] * p.one + cs[K::WT_OFF + warp];
-#pragma unroll
-          for (int v = 1; v < P / 2; v++) {
-            const int hb = 31 - __clz(v);
-            x[v] = x[v ^ (1 << hb)] * p.one + tpv[hb];
-          }
-#pragma unroll
-          for (int v = 0; v < P / 2; v++) {
-            tmax[v] = vmax2(tmax[v], x[v]);
-            tmax[v + P / 2] = __viaddmax_u16x2(x[v], tpv[R - 2], tmax[v + P / 2]);
+            for (int v = 0; v < P / 2; v++) {
+              tmax[v] = vmax2(tmax[v], x[v]);
+              tmax[v + P / 2] = __viaddmax_u16x2(x[v], tx[R - 2], tmax[v + P / 2]);
+            }
           }
         }
       };
@@ -428,7 +446,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         }
         const uint32_t field = (mv >> (16 * h)) & 0xFFFFu;
         const uint32_t rw = (uint32_t)h | ((uint32_t)v << 1) | role_hi;
-        const bool valid = nroles >= kRoles || (rw >> nroles) == 0u;
+        const bool valid = nroles >= K::ROLES || (rw >> nroles) == 0u;
         const bool cand = valid && field > 1u && (want_aux || !(field & 1u));
         if (!cand) {
           mv &= ~(0xFFFFu << (16 * h));
@@ -585,8 +603,8 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         ph[h] = ((mv >> (16 * h)) & 0xFFFFu) == 1u ? ax[h] : -1;
       }
       const uint32_t rw0 = ((uint32_t)v << 1) | role_hi;
-      const bool valid0 = nroles >= kRoles || (rw0 >> nroles) == 0u;
-      const bool valid1 = nroles >= kRoles || ((rw0 | 1u) >> nroles) == 0u;
+      const bool valid0 = nroles >= K::ROLES || (rw0 >> nroles) == 0u;
+      const bool valid1 = nroles >= K::ROLES || ((rw0 | 1u) >> nroles) == 0u;
       if (!valid0) continue;
       const uint32_t e0 = (rw0 & role_mask) | ehigh;
       const unsigned long long g0 = interleave(e0, o);
@@ -627,8 +645,8 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       for (int v = 0; v < P; v++) {
         int ph[2], ax[2];
         const uint32_t rw0 = ((uint32_t)v << 1) | role_hi;
-        const bool valid0 = nroles >= kRoles || (rw0 >> nroles) == 0u;
-        const bool valid1 = nroles >= kRoles || ((rw0 | 1u) >> nroles) == 0u;
+        const bool valid0 = nroles >= K::ROLES || (rw0 >> nroles) == 0u;
+        const bool valid1 = nroles >= K::ROLES || ((rw0 | 1u) >> nroles) == 0u;
         if (!valid0) continue;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -714,6 +732,17 @@ int shape_grid_or_launch(const hp::PhenParams& prm, cudaStream_t stream, unsigne
 
 namespace hp {
 
+void small_roles_shape(int max_ne_free, int* roles, int* reg_bits, int* tile) {
+  *roles = max_ne_free >= kRoles ? kRoles : std::max(max_ne_free, 11);
+  if (*roles == 13 || *roles == 12) {
+    *reg_bits = 5;
+    *tile = 128;
+  } else if (*roles == 11) {
+    *reg_bits = 4;
+    *tile = 64;
+  }
+}
+
 bool tile_cfg_supported(int reg_bits, int tile) {
   switch (reg_bits * 1000 + tile) {
     case 4064: case 4128: case 5064: case 5128: case 5256: case 6064: case 6128: case 6256:
@@ -733,6 +762,14 @@ int grid_or_launch(const PhenParams& prm, int reg_bits, int tile, cudaStream_t s
                    unsigned* grid, bool launch) {
   // thresholds above 1 have one compiled shape (the default)
   if (prm.gap2 > 2u) return shape_grid_or_launch<Cfg<5, 256>, true>(prm, stream, grid_limit, grid, launch);
+  // fewer roles per CTA: one compiled shape each (small_roles_shape)
+  switch (prm.roles) {
+    case 13: return shape_grid_or_launch<Cfg<5, 128, 13>>(prm, stream, grid_limit, grid, launch);
+    case 12: return shape_grid_or_launch<Cfg<5, 128, 12>>(prm, stream, grid_limit, grid, launch);
+    case 11: return shape_grid_or_launch<Cfg<4, 64, 11>>(prm, stream, grid_limit, grid, launch);
+    case kRoles: break;
+    default: return fail(HP_EINVAL, "unsupported role count");
+  }
   switch (reg_bits * 1000 + tile) {
     case 4064: return shape_grid_or_launch<Cfg<4, 64>>(prm, stream, grid_limit, grid, launch);
     case 4128: return shape_grid_or_launch<Cfg<4, 128>>(prm, stream, grid_limit, grid, launch);
@@ -809,7 +846,9 @@ int half_tables(const hp_structs* cs, DevTables** out) {
 }
 
 int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
-                   int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm) {
+                   int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm, int roles) {
+  if (roles != kRoles && roles != 13 && roles != 12 && roles != 11) return fail(HP_EINVAL, "unsupported role count");
+  prm.roles = roles;
   if (n < 1 || n > kPhenMaxInst)
     return fail(HP_EINVAL, "a batch holds 1 to " + std::to_string(kPhenMaxInst) + " instances");
   // instances with more conformations first, so the dynamic queue ends on cheap items
@@ -863,7 +902,7 @@ int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const 
       d.item_begin = items;
       d.ne_free = (unsigned)std::min((m + 1) / 2, s->NE);
       d.no_free = (unsigned)std::min(m / 2, s->NO);
-      d.nroles = (unsigned)std::min((int)d.ne_free, kRoles);
+      d.nroles = (unsigned)std::min((int)d.ne_free, roles);
       d.inst = (unsigned)q;
       d.otab = nullptr;
       d.ntab = 0;
@@ -887,18 +926,74 @@ int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const 
   return HP_OK;
 }
 
+int role_classes(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
+                 int32_t* const* d_phen, int tile, std::vector<int>& cls) {
+  PhenParams* tmp = new (std::nothrow) PhenParams();
+  if (!tmp) return fail(HP_ENOMEM, "out of host memory");
+  cls.assign(n, kRoles);
+  for (int i = 0; i < n; i++) {
+    const int rc = plan_phenotype(&libs[i], &begins[i], &counts[i], 1, &d_phen[i], nullptr, tile, *tmp);
+    if (rc != HP_OK) {
+      delete tmp;
+      return rc;
+    }
+    int max_ne = 0, r = 0, t = 0;
+    for (int k = 0; k < tmp->nblocks; k++) max_ne = std::max(max_ne, (int)tmp->blocks[k].ne_free);
+    small_roles_shape(max_ne, &cls[i], &r, &t);
+  }
+  delete tmp;
+  return HP_OK;
+}
+
 int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
                   int32_t* const* d_phen, int32_t* const* d_aux, int reg_bits, int tile, cudaStream_t st,
-                  unsigned grid_limit, int gap_threshold) {
+                  unsigned grid_limit, int gap_threshold, bool auto_roles) {
   if (!tile_cfg_supported(reg_bits, tile)) return fail(HP_EINVAL, "unsupported tile configuration");
   if (gap_threshold < 1 || gap_threshold > (1 << 20)) return fail(HP_EINVAL, "gap_threshold must be in [1, 2^20]");
   if (gap_threshold > 1) {
     reg_bits = 5;  // the shape compiled for thresholds above 1
     tile = 256;
+    auto_roles = false;
+  }
+  if (auto_roles && n > 1) {
+    // boxes that need different role counts: one persistent launch per role count, each over all the
+    // boxes of that count, back to back on the stream
+    std::vector<int> cls;
+    int rc = role_classes(libs, begins, counts, n, d_phen, tile, cls);
+    if (rc != HP_OK) return rc;
+    if (std::any_of(cls.begin(), cls.end(), [&](int c) { return c != cls[0]; })) {
+      for (const int c : {kRoles, 13, 12, 11}) {
+        std::vector<const hp_structs*> l;
+        std::vector<uint64_t> b, k;
+        std::vector<int32_t*> o, a;
+        for (int i = 0; i < n; i++)
+          if (cls[i] == c) {
+            l.push_back(libs[i]);
+            b.push_back(begins[i]);
+            k.push_back(counts[i]);
+            o.push_back(d_phen[i]);
+            a.push_back(d_aux ? d_aux[i] : nullptr);
+          }
+        if (l.empty()) continue;
+        rc = run_phenotype(l.data(), b.data(), k.data(), (int)l.size(), o.data(), d_aux ? a.data() : nullptr, reg_bits,
+                           tile, st, grid_limit, gap_threshold, true);
+        if (rc != HP_OK) return rc;
+      }
+      return HP_OK;
+    }
   }
   PhenParams* prm = new (std::nothrow) PhenParams();
   if (!prm) return fail(HP_ENOMEM, "out of host memory");
   int rc = plan_phenotype(libs, begins, counts, n, d_phen, d_aux, tile, *prm);
+  if (rc == HP_OK && auto_roles) {
+    // every block has fewer than 14 free even residues (a small box or a short range): a shape with
+    // as many roles per CTA as there are, so that no CTA evaluates patterns it then drops
+    int max_ne = 0;
+    for (int i = 0; i < prm->nblocks; i++) max_ne = std::max(max_ne, (int)prm->blocks[i].ne_free);
+    int roles = kRoles;
+    small_roles_shape(max_ne, &roles, &reg_bits, &tile);
+    if (roles != kRoles) rc = plan_phenotype(libs, begins, counts, n, d_phen, d_aux, tile, *prm, roles);
+  }
   prm->gap2 = 2u * (uint32_t)gap_threshold;
   if (rc != HP_OK || prm->total_items == 0) {
     delete prm;
@@ -951,7 +1046,8 @@ extern "C" int hp_phenotype_map(const hp_structs* s, uint64_t seq_begin, uint64_
   if (seq_begin >= space || seq_count > space - seq_begin)
     return hp::fail(HP_EINVAL, "hp_phenotype_map: sequence range exceeds 2^N");
   int r = s->tile_reg_bits, t = s->tile_size;
+  const bool auto_roles = r == 0;  // no shape set on the library: pick the role count from the range
   if (!r) hp::default_tile_cfg(&r, &t);
   return hp::run_phenotype(&s, &seq_begin, &seq_count, 1, &d_phen, d_argmin_aux ? &d_argmin_aux : nullptr, r, t,
-                           (cudaStream_t)stream, 0, gap_threshold);
+                           (cudaStream_t)stream, 0, gap_threshold, auto_roles);
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "hp_internal.h"
 
@@ -49,12 +50,20 @@ struct PhenParams {
   // pass-2 work lists: wl_ctas lists of wl_stride uint16 each (2^14 entries + max ntiles + 1 offsets)
   uint16_t* wlist;
   unsigned wl_stride, wl_ctas;
+  int roles;  // even-pattern bits per CTA of the plan (selects the compiled shape)
 };
 
 bool tile_cfg_supported(int reg_bits, int tile);
 void default_tile_cfg(int* reg_bits, int* tile);
+// roles: even-pattern bits per CTA (14, or 13 / 12 / 11 for the small-role shapes)
 int plan_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
-                   int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm);
+                   int32_t* const* d_phen, int32_t* const* d_aux, int tile, PhenParams& prm, int roles = 14);
+// The compiled shape for blocks with at most max_ne_free free even residues: *roles = 14 (shape
+// unchanged) or 13 / 12 / 11 with their own (reg_bits, tile).
+void small_roles_shape(int max_ne_free, int* roles, int* reg_bits, int* tile);
+// The role count each entry would get on its own (small_roles_shape of its blocks), into cls.
+int role_classes(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
+                 int32_t* const* d_phen, int tile, std::vector<int>& cls);
 int launch_phenotype(const PhenParams& prm, int reg_bits, int tile, cudaStream_t stream, unsigned grid_limit);
 // Device block a launch needs (control words, then one pass-2 work list per CTA): its size and the
 // number of CTAs the launch will use; bind_launch_block points prm.ctrl / prm.wlist into it.  The
@@ -64,8 +73,9 @@ int launch_block_bytes(const PhenParams& prm, int reg_bits, int tile, unsigned g
 void bind_launch_block(PhenParams& prm, void* block, unsigned ctas);
 // plan + per-call control words + launch + error read-back (synchronises the stream); a
 // gap_threshold above 1 runs the one shape compiled for it (reg_bits 5, tile 256)
+// (auto_roles: use a small-role shape when every block has fewer than 14 free even residues)
 int run_phenotype(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int n,
                   int32_t* const* d_phen, int32_t* const* d_aux, int reg_bits, int tile, cudaStream_t st,
-                  unsigned grid_limit, int gap_threshold = 1);
+                  unsigned grid_limit, int gap_threshold = 1, bool auto_roles = false);
 
 }  // namespace hp

@@ -251,3 +251,26 @@ def test_designability_odd_sizes_and_bad_entries(hp):
     bad = torch.tensor([0, 1, 7, -1], dtype=torch.int32, device="cuda")
     with pytest.raises(hp.HPError):
         hp.designability(bad, 7)
+
+
+@pytest.mark.parametrize("dims,begin,bits", [((3, 3, 3), 1 << 26, 26), ((3, 3, 3), 3 << 24, 24), ((3, 3, 3), 5 << 22, 22),
+                                             ((3, 3, 3), 7 << 20, 20), ((5, 5), 0, 25), ((2, 3, 4), 0, 24),
+                                             ((4, 5), 0, 20), ((6, 6), 9 << 26, 26)])
+def test_small_role_shapes_equal_the_14_role_shape(hp, obox, dims, begin, bits):
+    """Blocks with fewer than 14 free even residues run a shape with as many roles per CTA as there are
+    (13, 12 or 11); the map equals the default shape's (forced by setting it on the library) id by id,
+    and the oracle on a sample."""
+    n = 1 << bits
+    s = hp.Structs(dims)
+    auto = hp.phenotype_map(s, begin, n)
+    aux_auto = torch.empty(n, dtype=torch.int32, device="cuda")
+    hp.phenotype_map(s, begin, n, out=torch.empty_like(auto), aux=aux_auto)
+    s.set_tile_cfg(5, 256)
+    fixed = hp.phenotype_map(s, begin, n)
+    aux_fixed = torch.empty(n, dtype=torch.int32, device="cuda")
+    hp.phenotype_map(s, begin, n, out=torch.empty_like(fixed), aux=aux_fixed)
+    assert torch.equal(auto, fixed)
+    assert torch.equal(aux_auto, aux_fixed)
+    off = inputs.sample_ids(bits, 300, seed=bits + 17)
+    np.testing.assert_array_equal(auto.cpu().numpy()[off.astype(np.int64)],
+                                  obox(dims).phenotypes(off + np.uint64(begin)))
