@@ -31,6 +31,8 @@ WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformatio
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full 3x3x3 phenotype-kernel launch, from
 # an ncu capture of the current kernel; None whenever the kernel has changed since the last capture.
 TRAFFIC_PER_LAUNCH = None
+# ALU lane-ops per sequence x conformation evaluation of the map kernel's pass 1 (default shape)
+ALU_OPS_PER_EVAL = 24 / 64
 
 
 def dist_env():
@@ -244,6 +246,33 @@ def run_stream(args):
     return 0
 
 
+def run_stream_components(args):
+    """Neutral-network counts of the whole space of a box through shards (hp_stream_components)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2008_05612_gb300 as hp
+
+    parts = args.stream_components.split(":")
+    dims = tuple(int(x) for x in parts[0].split("x"))
+    bits = int(parts[1])
+    window = int(parts[2]) if len(parts) > 2 and parts[2] else None
+    s = hp.Structs(dims)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ncomp, computed = hp.stream_components(s, bits, window=window)
+    dt = time.perf_counter() - t0
+    nz = ncomp[ncomp > 0]
+    print(json.dumps({"case": f"stream components {args.stream_components}", "box": parts[0], "N": s.N, "S": s.S,
+                      "shards": 1 << bits, "maps_computed": computed, "seconds": dt,
+                      "components": int(ncomp.sum()), "phenotypes_with_components": int(nz.size),
+                      "max_components_of_a_phenotype": int(ncomp.max()),
+                      "phenotypes_with_one_component": int((ncomp == 1).sum())}))
+    return 0
+
+
 def run_map_only(args):
     """Phenotype map of one aligned id block, W + K launches, CUDA-event timed (a small case for ncu)."""
     import torch
@@ -292,14 +321,14 @@ def map_block_6x6(hp, torch, peak_ops: float, bits: int = 27, reps: int = 3):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     evals = n * s.S_dir
-    achieved = 0.5 * evals / (ms * 1e-3)
+    achieved = ALU_OPS_PER_EVAL * evals / (ms * 1e-3)
     folded = int((phen >= 0).sum().item())
     return {"workload": f"6x6 phenotype map of ids [0, 2^{bits}) x {s.S_dir} conformations ({s.S} classes)",
             "map_ms": ms, "evals_per_s": evals / (ms * 1e-3), "sequences_per_s": n / (ms * 1e-3),
             "fold_fraction": folded / n,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "ALU lane-ops/s",
                          "frac": achieved / peak_ops, "kernel": "phenotype_kernel<Cfg<5,256>, false>",
-                         "note": "0.5 packed max per performed evaluation (all 2^27 ids of the block are evaluated)"}}
+                         "note": "0.375 ALU lane-ops per performed evaluation (all 2^27 ids of the block are evaluated)"}}
 
 
 BATCH_BOXES = ((4, 4), (4, 5), (5, 5), (2, 3, 4), (3, 3, 3))
@@ -516,6 +545,8 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (one JSON line)")
     ap.add_argument("--stream", default=None, metavar="BOX:BITS[:WINDOW[:DIR]]",
                     help="whole-space map of BOX in 2^BITS shards with exact designability and Eq. 2 statistics")
+    ap.add_argument("--stream-components", default=None, metavar="BOX:BITS[:WINDOW]",
+                    help="neutral-network counts per phenotype over the whole space of BOX from 2^BITS shards")
     ap.add_argument("--train-case", action="store_true",
                     help="time the proposal network's training step alone (batch 4096, 3x3x3 classes)")
     ap.add_argument("--proposal-case", action="store_true",
@@ -541,6 +572,8 @@ def main():
         return 0
     if args.stream:
         return run_stream(args)
+    if args.stream_components:
+        return run_stream_components(args)
 
     import torch
 
@@ -675,16 +708,18 @@ def main():
     peaks = measured_peaks()
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    # ALU-pipe roofline of the phenotype kernel: every evaluation needs at least half a packed
-    # 16x2 max (two sequences per max.u16x2 / fused add+max), and the ALU pipe retires
-    # 64 lane-ops per clock per SM (16 lanes x 4 sub-partitions) on 152 SMs.
+    # ALU-pipe roofline of the phenotype kernel.  Its ALU work per evaluation, counted from the
+    # source: per thread, two conformations x 32 sequences (16 packed registers) take 8 three-input
+    # packed maxes and 16 fused add + max, i.e. ALU_OPS_PER_EVAL lane-ops per evaluation (the
+    # subset-sum additions are IMADs on the FMA pipe).  The ALU pipe retires 64 lane-ops per clock
+    # per SM for these instructions (probed with operands that change every iteration) on 152 SMs.
     peak_ops = 64 * 152 * sm_max * 1e6
     map_avg_ms = float(np.mean(map_ms))
     map_evals = evals_step / (map_avg_ms * 1e-3)
     # evaluations the kernel actually performs: for an odd-length chain the full map is computed for one
     # id of each reversal pair (odd-residue patterns o <= reverse(o)) and mirrored
     performed = performed_sequences(N) * Sdir
-    achieved = 0.5 * performed / (map_avg_ms * 1e-3)
+    achieved = ALU_OPS_PER_EVAL * performed / (map_avg_ms * 1e-3)
     tile_cfg = s.tile_cfg()
     line = {
         "metric": METRIC,
@@ -717,11 +752,12 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "ALU lane-ops/s",
                      "frac": achieved / peak_ops, "traffic": TRAFFIC_PER_LAUNCH,
                      "kernel": f"phenotype_kernel<Cfg<{tile_cfg[0]},{tile_cfg[1]}>, false>",
-                     "peak_source": "derived: 64 ALU lane-ops/clk/SM x 152 SMs x max SM clock (no integer peak is measured "
-                                    "by the driver)",
-                     "note": "algorithmic ALU work = 0.5 packed max per performed sequence x conformation evaluation "
-                             "(odd chains: one id of each reversal pair, 50.8% of 2^27 for 3x3x3); achieved uses the "
-                             "map kernel's CUDA-event time inside the step"},
+                     "peak_source": "64 ALU lane-ops/clk/SM (max.u16x2, three-input max and fused add+max each measured "
+                                    "at 63.5 lane-ops/clk/SM on GB300 by a throughput probe) x 152 SMs x max SM clock",
+                     "note": "ALU work = 0.375 lane-ops per performed sequence x conformation evaluation (8 three-input "
+                             "packed maxes + 16 fused add+max per 2 conformations x 32 sequences per thread), counted from "
+                             "the kernel source; odd chains evaluate one id of each reversal pair (50.8% of 2^27 for "
+                             "3x3x3); achieved uses the map kernel's CUDA-event time inside the step"},
         "clocks": clocks,
     }
     if rank == 0:

@@ -152,12 +152,13 @@ struct Cfg {
   static_assert(NW >= 4, "warp tables are written in groups of four");
 };
 
-// Turn tile t's staged records (bulk copy issued two tiles ahead) into this CTA's coefficient
-// records in buffer t & 1: one thread per conformation.  P2: the pass-2 layout (stride CS2, 4-byte
-// stores) instead of pass 1's (stride CSTRIDE, 16-byte stores).  No barrier: the caller publishes
-// the records (mbarrier arrive); a bounded wait that gives up raises *s_abort.
+// Turn the staged records of tile `tile` (the t-th tile of this pass; its bulk copy was issued two
+// tiles ahead into raw buffer t & 1) into this CTA's coefficient records in buffer t & 1: one
+// thread per conformation.  P2: the pass-2 layout (stride CS2, 4-byte stores) instead of pass 1's
+// (stride CSTRIDE, 16-byte stores).  No barrier: the caller publishes the records (mbarrier
+// arrive); a bounded wait that gives up raises *s_abort.
 template <class K, bool P2 = false>
-__device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* err, int t, uint32_t* rawbuf,
+__device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* err, int t, int tile, uint32_t* rawbuf,
                                              uint32_t* coefbuf, uint64_t* bars,
                                              unsigned (&waited)[2], uint32_t o, uint32_t ehigh, int nroles,
                                              int* s_abort, long long spin) {
@@ -173,7 +174,7 @@ __device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* e
     } else {
       const uint32_t* r = rawbuf + buf * T * in.rec_words + tid * in.rec_words;
       uint32_t* c = cbuf + tid * STRIDE;
-      const int s = t * T + tid;
+      const int s = tile * T + tid;
       if (s < in.S_dir) {
         uint32_t a[K::ROLES];
 #pragma unroll
@@ -239,14 +240,15 @@ __device__ __forceinline__ void produce_work(const hp::PhenInst& in, unsigned* e
   waited[buf]++;
 }
 
+// Bulk copies of the first two tiles of a pass (tiles t0 and t1; t1 < 0: the pass has one tile).
 template <int T>
 __device__ __forceinline__ void prefetch_first_tiles(const hp::PhenInst& in, uint32_t* rawbuf, uint64_t* bars,
-                                                     unsigned (&issued)[2]) {
+                                                     unsigned (&issued)[2], int t0, int t1) {
   const unsigned raw_bytes = (unsigned)(T * in.rec_words * 4);
-  if (threadIdx.x == 0) bulk_load(rawbuf, in.rec, raw_bytes, &bars[0]);
+  if (threadIdx.x == 0) bulk_load(rawbuf, in.rec + (size_t)t0 * T * in.rec_words, raw_bytes, &bars[0]);
   issued[0]++;
-  if (in.ntiles > 1) {
-    if (threadIdx.x == 0) bulk_load(rawbuf + T * in.rec_words, in.rec + (size_t)T * in.rec_words, raw_bytes, &bars[1]);
+  if (t1 >= 0) {
+    if (threadIdx.x == 0) bulk_load(rawbuf + T * in.rec_words, in.rec + (size_t)t1 * T * in.rec_words, raw_bytes, &bars[1]);
     issued[1]++;
   }
 }
@@ -316,13 +318,14 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     for (int v = 0; v < P; v++) tmax[v] = m1[v] = ts[v] = 0u;
     if (GAP)
       for (int v = 0; v < P; v++) st_best[v * kThreads + tid] = 0u;  // 0: no other tile yet
-    prefetch_first_tiles<T>(in, rawbuf, bars, issued);
+    prefetch_first_tiles<T>(in, rawbuf, bars, issued, 0, in.ntiles > 1 ? 1 : -1);
     // coefficient records of tile t + 1 are produced halfway through the consumption of tile t
     // (double buffered).  No CTA barrier: the producer warps arrive on full[b] when a buffer is
     // written, every warp arrives on empty[b] when it has consumed it, and a warp waits only for
     // the buffer it needs next, so fast warps run ahead instead of idling at a barrier.
     const bool producer = tid < T;
-    auto produce_and_publish = [&](int tp, auto p2) {
+    // the tp-th tile of the pass, `tile` (pass 1: every tile, tile = tp; pass 2: the listed ones)
+    auto produce_and_publish = [&](int tp, int tile, auto p2) {
       const int b = tp & 1;
       if (producer) {
         // the previous contents of buffer b (tile tp - 2) must have been consumed by every warp
@@ -331,8 +334,8 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
           s_abort = 1;
         }
       }
-      produce_work<K, decltype(p2)::value>(in, p.ctrl, tp, rawbuf, coefbuf, bars, waited, o, ehigh, nroles, &s_abort,
-                                           p.spin);
+      produce_work<K, decltype(p2)::value>(in, p.ctrl, tp, tile, rawbuf, coefbuf, bars, waited, o, ehigh, nroles,
+                                           &s_abort, p.spin);
       if (producer) {
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bars[2 + b])) : "memory");
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     };
     using Pass1Layout = std::false_type;
     using Pass2Layout = std::true_type;
-    produce_and_publish(0, Pass1Layout{});
+    produce_and_publish(0, 0, Pass1Layout{});
     for (int t = 0; t < in.ntiles; t++) {
       const int b = t & 1;
       if (!mbar_wait(&bars[2 + b], (b ? fcnt1 : fcnt0) & 1u, p.spin_handover)) {
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         }
       };
       consume(0, T / 2);
-      if (t + 1 < in.ntiles) produce_and_publish(t + 1, Pass1Layout{});
+      if (t + 1 < in.ntiles) produce_and_publish(t + 1, t + 1, Pass1Layout{});
       consume(T / 2, T);
       // this warp is done with buffer b
       __syncwarp();
@@ -464,7 +467,8 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     // shared-memory atomics in the idle coefficient area.  Every warp then takes a share of each
     // tile's candidates, whoever owns them, so no warp holds up the others with a long list.
     uint16_t* wl = p.wlist + (size_t)blockIdx.x * p.wl_stride;
-    uint16_t* woff = wl + (1u << kRoles);  // ntiles + 1 offsets
+    uint16_t* woff = wl + (1u << kRoles);      // ntiles + 1 offsets
+    uint16_t* wtiles = woff + in.ntiles + 1;  // the tiles that hold candidates, ascending; then their count
     unsigned* whist = coefbuf;
     for (int i = tid; i <= in.ntiles; i += kThreads) whist[i] = 0u;
     __syncthreads();
@@ -485,13 +489,26 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
         if (lane >= d) incl += y;
       }
-      unsigned at = incl - run;
+      unsigned at = incl - run, nonempty = 0;
       for (int i = i0; i < i1; i++) {
         const unsigned c = whist[i];
         woff[i] = (uint16_t)at;
         whist[i] = at;  // becomes the placement cursor
         at += c;
+        nonempty += (i < in.ntiles && c != 0u) ? 1u : 0u;
       }
+      __syncwarp();  // whist now holds the offsets: tile i has whist[i + 1] - whist[i] candidates
+      // the tiles that hold candidates, ascending, and their number at wtiles[ntiles]
+      unsigned nincl = nonempty;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, nincl, d);
+        if (lane >= d) nincl += y;
+      }
+      unsigned w = nincl - nonempty;
+      for (int i = i0; i < min(i1, in.ntiles); i++)
+        if (whist[i + 1] != whist[i]) wtiles[w++] = (uint16_t)i;
+      if (lane == 31) wtiles[in.ntiles] = (uint16_t)nincl;
     }
     __syncthreads();
     for (unsigned long long m = cmask; m; m &= m - 1) {
@@ -507,10 +524,15 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
     // ================= pass 2: re-stage each tile and resolve its candidates.  The records of
     // tile t + 1 are produced (pass-2 layout) before tile t is resolved, with the hand-over of pass 1
     // (produced / consumed mbarriers).
-    prefetch_first_tiles<T>(in, rawbuf, bars, issued);
-    produce_and_publish(0, Pass2Layout{});
-    for (int t = 0; t < in.ntiles; t++) {
-      const int b = t & 1;
+    // only the tiles that hold candidates are staged and produced again
+    const int n2 = wtiles[in.ntiles];
+    if (n2 > 0) {
+      prefetch_first_tiles<T>(in, rawbuf, bars, issued, wtiles[0], n2 > 1 ? (int)wtiles[1] : -1);
+      produce_and_publish(0, wtiles[0], Pass2Layout{});
+    }
+    for (int i2 = 0; i2 < n2; i2++) {
+      const int b = i2 & 1;
+      const int t = wtiles[i2];
       if (!mbar_wait(&bars[2 + b], (b ? fcnt1 : fcnt0) & 1u, p.spin_handover)) {
         atomicOr(p.ctrl, kErrTimeout);
         s_abort = 1;
@@ -518,14 +540,14 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       if (b) fcnt1++;
       else fcnt0++;
       if (s_abort) break;
-      // every producer has read raw[b] (tile t): refill it with tile t + 2
-      if (t + 2 < in.ntiles) {
+      // every producer has read raw[b] (the i2-th listed tile): refill it with the (i2 + 2)-th
+      if (i2 + 2 < n2) {
         if (tid == 0)
-          bulk_load(rawbuf + b * T * in.rec_words, in.rec + (size_t)(t + 2) * T * in.rec_words,
+          bulk_load(rawbuf + b * T * in.rec_words, in.rec + (size_t)wtiles[i2 + 2] * T * in.rec_words,
                     (unsigned)(T * in.rec_words * 4), &bars[b]);
         issued[b]++;
       }
-      if (t + 1 < in.ntiles) produce_and_publish(t + 1, Pass2Layout{});
+      if (i2 + 1 < n2) produce_and_publish(i2 + 1, wtiles[i2 + 1], Pass2Layout{});
       const uint32_t* cbuf = coefbuf + b * T * K::CS2;
       const int e1 = woff[t + 1];
       for (int e = woff[t] + warp; e < e1; e += K::NW) {
@@ -795,7 +817,8 @@ int launch_block_bytes(const PhenParams& prm, int reg_bits, int tile, unsigned g
   if (rc != HP_OK) return rc;
   int max_tiles = 0;
   for (int i = 0; i < prm.ninst; i++) max_tiles = std::max(max_tiles, prm.inst[i].ntiles);
-  const size_t stride = ((size_t)(1u << kRoles) + (size_t)max_tiles + 1 + 63) / 64 * 64;  // uint16, 128-byte rows
+  // uint16: 2^14 entries, ntiles + 1 offsets, ntiles + 1 listed tiles and their count; 128-byte rows
+  const size_t stride = ((size_t)(1u << kRoles) + 2 * ((size_t)max_tiles + 1) + 63) / 64 * 64;
   *ctas = grid;
   *bytes = 256 + stride * 2 * grid;
   return HP_OK;
@@ -806,7 +829,7 @@ void bind_launch_block(PhenParams& prm, void* block, unsigned ctas) {
   for (int i = 0; i < prm.ninst; i++) max_tiles = std::max(max_tiles, prm.inst[i].ntiles);
   prm.ctrl = static_cast<unsigned*>(block);
   prm.wlist = reinterpret_cast<uint16_t*>(static_cast<char*>(block) + 256);
-  prm.wl_stride = (unsigned)(((size_t)(1u << kRoles) + (size_t)max_tiles + 1 + 63) / 64 * 64);
+  prm.wl_stride = (unsigned)(((size_t)(1u << kRoles) + 2 * ((size_t)max_tiles + 1) + 63) / 64 * 64);
   prm.wl_ctas = ctas;
 }
 

@@ -47,7 +47,8 @@ struct PhenParams {
   uint32_t gap2;       // 2 x the energy-gap threshold (2: strict uniqueness, the paper's threshold 1)
   long long spin;           // polls of a bulk-copy wait before it gives up (hp_set_wait_limit)
   long long spin_handover;  // polls of a coefficient-buffer hand-over wait before it gives up
-  // pass-2 work lists: wl_ctas lists of wl_stride uint16 each (2^14 entries + max ntiles + 1 offsets)
+  // pass-2 work lists: wl_ctas lists of wl_stride uint16 each (2^14 entries, max ntiles + 1 offsets,
+  // the listed tiles that hold candidates and their count)
   uint16_t* wlist;
   unsigned wl_stride, wl_ctas;
   int roles;  // even-pattern bits per CTA of the plan (selects the compiled shape)
