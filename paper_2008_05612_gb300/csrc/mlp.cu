@@ -713,11 +713,14 @@ int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, int n, int rows
   return rc;
 }
 
-// refresh the bf16 copies and transposes used by the forward and backward GEMMs
-void refresh_copies(hp_mlp* m, cudaStream_t st) {
-  cast_bf16<<<grid_for(m->n[0]), 256, 0, st>>>(m->w[0], m->w1b, m->n[0]);
-  cast_bf16<<<grid_for(m->n[2]), 256, 0, st>>>(m->w[2], m->w2b, m->n[2]);
-  cast_bf16<<<grid_for(m->n[4]), 256, 0, st>>>(m->w[4], m->w3b, m->n[4]);
+// refresh the bf16 copies and transposes used by the forward and backward GEMMs (cast: also the
+// plain bf16 copies, which the optimizer step writes itself)
+void refresh_copies(hp_mlp* m, cudaStream_t st, bool cast = true) {
+  if (cast) {
+    cast_bf16<<<grid_for(m->n[0]), 256, 0, st>>>(m->w[0], m->w1b, m->n[0]);
+    cast_bf16<<<grid_for(m->n[2]), 256, 0, st>>>(m->w[2], m->w2b, m->n[2]);
+    cast_bf16<<<grid_for(m->n[4]), 256, 0, st>>>(m->w[4], m->w3b, m->n[4]);
+  }
   transpose(m->w2b, m->H1, m->H2, m->H1, m->w2t, m->H2, m->H2, st);
   transpose(m->w3b, m->H2, m->S, m->H2, m->w3t, m->Spad, m->Spad, st);
   gather_rows<<<grid_for((size_t)m->S * (m->H2 / 8)), 256, 0, st>>>(m->w3b, m->w[5], m->perm, m->S, m->H2, m->w3p, m->b3p);
@@ -914,10 +917,12 @@ extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t
   m->steps++;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float c1 = 1.f / (1.f - powf(b1, (float)m->steps)), c2 = 1.f / (1.f - powf(b2, (float)m->steps));
+  // the weight matrices' bf16 copies are written by the update itself
+  bf16* const wb[6] = {m->w1b, nullptr, m->w2b, nullptr, m->w3b, nullptr};
   for (int i = 0; i < 6; i++)
-    adam_update<<<grid_for(m->n[i]), 256, 0, st>>>(m->w[i], m->g[i], m->m[i], m->v[i], nullptr, m->n[i], lr, b1, b2, eps,
+    adam_update<<<grid_for(m->n[i]), 256, 0, st>>>(m->w[i], m->g[i], m->m[i], m->v[i], wb[i], m->n[i], lr, b1, b2, eps,
                                                      c1, c2);
-  refresh_copies(m, st);
+  refresh_copies(m, st, false);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_train_step: launch");
   if (h_loss) {

@@ -128,6 +128,15 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// four floats as four bf16 in one 8-byte store (dst 8-byte aligned)
+__device__ __forceinline__ void store_bf16x4(bf16* dst, float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  uint2 u;
+  u.x = *reinterpret_cast<const uint32_t*>(&lo);
+  u.y = *reinterpret_cast<const uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(dst) = u;
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%"
@@ -368,21 +377,34 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
                 have_zl = true;
               }
             } else {
-              // dz = (softmax - onehot) * scale; transposed stores straight from the row layout
-              // (lanes = 32 consecutive rows of one column), row-major ones through the square
+              // dz = (softmax - onehot) * scale into the padded square (row = lane), then both
+              // layouts are written from it: a full 32 x 32 block four bf16 per lane and store
+              // (8-byte stores, 256 bytes per warp instruction), a ragged one element by element
 #pragma unroll
               for (int j = 0; j < 32; j++) {
                 const int col = cbase + j;
                 float d = 0.f;
                 if (lab >= 0 && j < cmax) d = (__expf(__uint_as_float(v[j]) - rm) * rs - (col == lab ? 1.f : 0.f)) * ep.scale;
                 area[lane * 33 + j] = d;
-                if (j < cmax && my_row < p.M) ep.dzt[(size_t)col * ep.ldzt + my_row] = __float2bfloat16(d);
               }
               __syncwarp();
-              if (lane < cmax) {
-                const int rmax = min(32, p.M - rbase);
-                for (int r = 0; r < rmax; r++)
-                  ep.dz[(size_t)(rbase + r) * ep.ldz + cbase + lane] = __float2bfloat16(area[r * 33 + lane]);
+              const int rmax = min(32, p.M - rbase);
+              if (cmax == 32 && rmax == 32) {
+                const int sub = lane >> 3, quad = (lane & 7) * 4;
+#pragma unroll
+                for (int r = 0; r < 32; r += 4) {
+                  const float* a = area + (r + sub) * 33 + quad;  // row r + sub, columns quad .. + 3
+                  store_bf16x4(ep.dz + (size_t)(rbase + r + sub) * ep.ldz + cbase + quad, a[0], a[1], a[2], a[3]);
+                  const float* t = area + quad * 33 + (r + sub);  // column r + sub, rows quad .. + 3
+                  store_bf16x4(ep.dzt + (size_t)(cbase + r + sub) * ep.ldzt + rbase + quad, t[0], t[33], t[66], t[99]);
+                }
+              } else {
+                if (lane < cmax)
+                  for (int r = 0; r < rmax; r++)
+                    ep.dz[(size_t)(rbase + r) * ep.ldz + cbase + lane] = __float2bfloat16(area[r * 33 + lane]);
+                if (lane < rmax)
+                  for (int j = 0; j < cmax; j++)
+                    ep.dzt[(size_t)(cbase + j) * ep.ldzt + rbase + lane] = __float2bfloat16(area[lane * 33 + j]);
               }
               __syncwarp();
             }
