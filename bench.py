@@ -30,7 +30,7 @@ DIMS = (3, 3, 3)
 WORKLOAD = "3x3x3 full map: all 2^27 HP sequences x 103,346 directed conformations (51,704 classes)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full 3x3x3 phenotype-kernel launch, from
 # an ncu capture of the current kernel; None whenever the kernel has changed since the last capture.
-TRAFFIC_PER_LAUNCH = None
+TRAFFIC_PER_LAUNCH = 1_757_442_304
 # ALU lane-ops per sequence x conformation evaluation of the map kernel's pass 1 (default shape)
 ALU_OPS_PER_EVAL = 24 / 64
 

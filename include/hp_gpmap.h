@@ -140,6 +140,16 @@ int hp_autotune(hp_structs* s, hp_tile_cfg* best, float* ms, void* stream);
 int hp_phenotype_map_batch(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts, int32_t n,
                            int32_t* const* d_phen, const hp_tile_cfg* cfg, void* stream);
 
+/* The batched launch at an energy-gap threshold (Section 2.1; see
+ * hp_phenotype_map): entry i computes exactly what
+ * hp_phenotype_map(libs[i], begins[i], counts[i], gap_threshold, d_phen[i],
+ * NULL) would.  Thresholds above 1 run all boxes in one launch of the gap
+ * variant of the map kernel (its one compiled shape); 1 is
+ * hp_phenotype_map_batch with the default shapes.  gap_threshold outside
+ * [1, 2^20] gives HP_EINVAL.  Synchronises `stream`. */
+int hp_phenotype_map_batch_gap(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts,
+                               int32_t n, int32_t gap_threshold, int32_t* const* d_phen, void* stream);
+
 /* A batch captured once into a CUDA graph (queue reset + persistent launch).
  * Create uploads the tables and captures on a private stream; launch replays
  * the graph on `stream` without synchronising; status synchronises `stream`

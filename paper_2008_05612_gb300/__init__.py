@@ -24,7 +24,7 @@ _STATUS = {0: "HP_OK", -1: "HP_EINVAL", -2: "HP_ENOMEM", -3: "HP_ECUDA", -4: "HP
 EXPORTS = (
     "hp_enumerate_structures", "hp_structs_info", "hp_structs_export", "hp_structs_free",
     "hp_phenotype_map", "hp_set_tile_cfg", "hp_get_tile_cfg", "hp_tile_cfg_list", "hp_autotune",
-    "hp_phenotype_map_batch", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
+    "hp_phenotype_map_batch", "hp_phenotype_map_batch_gap", "hp_batch_plan_create", "hp_batch_plan_launch", "hp_batch_plan_status",
     "hp_batch_plan_free", "hp_sequence_scan", "hp_sequence_scan_gap", "hp_mlp_create", "hp_mlp_free", "hp_mlp_gradients",
     "hp_mlp_train_step", "hp_mlp_logits", "hp_mlp_topk", "hp_mlp_status", "hp_proposal_conformations", "hp_designability", "hp_designability_noalloc", "hp_robustness", "hp_neighbourhood", "hp_phi_matrix", "hp_robustness_cross", "hp_stream_shards", "hp_stream_components",
     "hp_neutral_components",
@@ -70,6 +70,7 @@ def lib():
         L.hp_tile_cfg_list.argtypes = [vp, vp]
         L.hp_autotune.argtypes = [vp, vp, vp, vp]
         L.hp_phenotype_map_batch.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.hp_phenotype_map_batch_gap.argtypes = [vp, vp, vp, i32, i32, vp, vp]
         L.hp_batch_plan_create.argtypes = [vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
         L.hp_batch_plan_launch.argtypes = [vp, vp]
         L.hp_batch_plan_status.argtypes = [vp, vp]
@@ -233,10 +234,16 @@ def _batch_args(structs, ranges, outs, cfg):
     return libs, begins, counts, n, ptrs, c
 
 
-def phenotype_map_batch(structs, ranges, outs, cfg=None, stream=None):
-    """One persistent launch for several boxes (hp_phenotype_map_batch); ranges = [(begin, count)]."""
+def phenotype_map_batch(structs, ranges, outs, cfg=None, stream=None, gap_threshold: int = 1):
+    """Batched persistent launches for several boxes (hp_phenotype_map_batch, or hp_phenotype_map_batch_gap
+    for gap_threshold > 1); ranges = [(begin, count)]."""
     libs, begins, counts, n, ptrs, c = _batch_args(structs, ranges, outs, cfg)
-    _check(lib().hp_phenotype_map_batch(libs, begins, counts, n, ptrs, c, _stream_ptr(stream)))
+    if gap_threshold == 1:
+        _check(lib().hp_phenotype_map_batch(libs, begins, counts, n, ptrs, c, _stream_ptr(stream)))
+    else:
+        if cfg is not None:
+            raise ValueError("a threshold above 1 runs the one compiled gap shape; cfg must be None")
+        _check(lib().hp_phenotype_map_batch_gap(libs, begins, counts, n, int(gap_threshold), ptrs, _stream_ptr(stream)))
     return outs
 
 

@@ -94,6 +94,18 @@ extern "C" int hp_phenotype_map_batch(const hp_structs* const* libs, const uint6
   return hp::run_phenotype(libs, begins, counts, n, d_phen, nullptr, r, t, (cudaStream_t)stream, 0, 1, auto_roles);
 }
 
+extern "C" int hp_phenotype_map_batch_gap(const hp_structs* const* libs, const uint64_t* begins, const uint64_t* counts,
+                                          int32_t n, int32_t gap_threshold, int32_t* const* d_phen, void* stream) {
+  if (!libs || !begins || !counts || !d_phen) return hp::fail(HP_EINVAL, "hp_phenotype_map_batch_gap: NULL argument");
+  if (n < 1) return hp::fail(HP_EINVAL, "hp_phenotype_map_batch_gap: empty batch");
+  if (gap_threshold < 1 || gap_threshold > (1 << 20))
+    return hp::fail(HP_EINVAL, "hp_phenotype_map_batch_gap: gap_threshold must be in [1, 2^20]");
+  int r = 0, t = 0;
+  hp::default_tile_cfg(&r, &t);
+  return hp::run_phenotype(libs, begins, counts, n, d_phen, nullptr, r, t, (cudaStream_t)stream, 0, gap_threshold,
+                           gap_threshold == 1);
+}
+
 extern "C" int hp_autotune(hp_structs* s, hp_tile_cfg* best, float* ms, void* stream) {
   if (!s) return hp::fail(HP_EINVAL, "hp_autotune: library is NULL");
   cudaStream_t st = (cudaStream_t)stream;

@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
         if constexpr (P <= 16) {
           // two conformations at a time: the lower half of the registers takes both with one
           // three-input packed max, the upper half with two fused add + max
-#pragma unroll 4
+#pragma unroll 8
           for (int s = s0; s < s1; s += 2) {
             uint32_t x[P / 2], y[P / 2], tx[K::TP_WORDS], ty[K::TP_WORDS];
             tree(cbuf + s * CSTRIDE, x, tx);
@@ -549,8 +549,36 @@ __global__ void __launch_bounds__(K::THREADS, 1) phenotype_kernel(const __grid_c
       }
       if (i2 + 1 < n2) produce_and_publish(i2 + 1, wtiles[i2 + 1], Pass2Layout{});
       const uint32_t* cbuf = coefbuf + b * T * K::CS2;
-      const int e1 = woff[t + 1];
-      for (int e = woff[t] + warp; e < e1; e += K::NW) {
+      const int e0 = woff[t], e1 = woff[t + 1];
+      // a tile with at least 32 candidates per warp: each lane scores one candidate against every
+      // conformation of the tile (no votes, independent steps); the rest one candidate per warp
+      const int nlane = (e1 - e0) / (32 * K::NW) * (32 * K::NW);
+      for (int base = e0 + 32 * warp; base < e0 + nlane; base += 32 * K::NW) {
+        const uint32_t ent = wl[base + lane];
+        const int owner = (int)(ent >> 6), c = (int)(ent & 63u), v = c >> 1, h = c & 1;
+        const int src = owner & 31, wo = owner >> 5;
+        const int fi = 2 * (v * kThreads + owner) + h;
+        const uint32_t sfld = best16[fi];
+        const uint32_t want = sfld & 0xFFFEu;
+        int count = 0, first = 0x7FFFFFFF;
+#pragma unroll 4
+        for (int sc = 0; sc < T; sc++) {
+          const uint32_t* cs = cbuf + sc * K::CS2;
+          uint32_t x = cs[src] + cs[K::WT_OFF + wo];
+#pragma unroll
+          for (int j = 0; j < R - 1; j++) x += ((v >> j) & 1) ? cs[K::TP_OFF + j] : 0u;
+          const uint32_t xf = (x >> (16 * h)) & 0xFFFFu;
+          if (xf == want) {  // padding scores 0 never match
+            first = min(first, sc);
+            if (!GAP) count++;
+          }
+          if (GAP && xf >= 2u && xf + p.gap2 > want) count++;
+        }
+        const bool unique = !(sfld & 1u) && count == 1;
+        best16[fi] = first != 0x7FFFFFFF ? (uint16_t)(((uint32_t)first << 1) | (unique ? 1u : 0u)) : (uint16_t)0;
+        if (first == 0x7FFFFFFF) tile16[fi] = 0xFFFFu;
+      }
+      for (int e = e0 + nlane + warp; e < e1; e += K::NW) {
         const uint32_t ent = wl[e];
         const int owner = (int)(ent >> 6), c = (int)(ent & 63u), v = c >> 1, h = c & 1;
         const int src = owner & 31, wo = owner >> 5;

@@ -136,3 +136,21 @@ def test_half_enumeration_equals_two_half_ranges(hp, obox, dims):
         want, want_aux = obox(dims).full_map(aux=True)
         np.testing.assert_array_equal(full.cpu().numpy(), want)
         np.testing.assert_array_equal(fa.cpu().numpy(), want_aux)
+
+
+@pytest.mark.parametrize("T", [2, 7])
+def test_batch_at_a_gap_threshold_equals_single_maps(hp, obox, T):
+    """hp_phenotype_map_batch_gap: several boxes at an energy-gap threshold T in one launch, equal to
+    the single maps at T (those are checked against the oracle's thresholds elsewhere), and to the
+    oracle on the small boxes."""
+    dims_list = [(4, 4), (4, 5), (2, 3, 4)]
+    structs = [hp.Structs(d) for d in dims_list]
+    ranges = [(0, 1 << s.N) for s in structs]
+    outs = [torch.full((1 << s.N,), -7, dtype=torch.int32, device="cuda") for s in structs]
+    hp.phenotype_map_batch(structs, ranges, outs, gap_threshold=T)
+    for d, s, o in zip(dims_list, structs, outs):
+        assert torch.equal(o, hp.phenotype_map(s, gap_threshold=T)), d
+        if s.N <= 20:
+            np.testing.assert_array_equal(o.cpu().numpy(), obox(d).full_map(gap=T))
+    with pytest.raises(hp.HPError):
+        hp.phenotype_map_batch(structs, ranges, outs, gap_threshold=(1 << 20) + 1)
