@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <new>
@@ -372,9 +373,9 @@ __global__ void softmax_xent(const float* __restrict__ Z, int ldz, int S, const 
   if (threadIdx.x == 0 && lab >= 0) atomicAdd(loss, logf(sum) + m - z[lab]);
 }
 
-// Column sums in two deterministic stages: part[chunk, c] = sum of the chunk's rows (256 rows per
+// Column sums in two deterministic stages: part[chunk, c] = sum of the chunk's rows (32 rows per
 // chunk, two columns per thread from bf16 pairs), then out[c] = sum of part[., c] in chunk order.
-constexpr int kColChunk = 256;
+constexpr int kColChunk = 32;
 __global__ void colsum_partial(const bf16* __restrict__ in, int ld, int rows, int cols, float* __restrict__ part) {
   const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (c >= cols) return;
@@ -393,12 +394,32 @@ __global__ void colsum_partial(const bf16* __restrict__ in, int ld, int rows, in
   if (c + 1 < cols) part[(size_t)blockIdx.y * cols + c + 1] = s1;
 }
 
+// 32 columns per block (lane = column): warp w sums the chunks w, w + 8, ... in order, then the
+// eight warp sums are added in warp order
 __global__ void colsum_final(const float* __restrict__ part, int chunks, int cols, float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+  __shared__ float ws[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int k = 0; k < chunks; k++) s += part[(size_t)k * cols + c];
-  out[c] = s;
+  if (c < cols)
+    for (int k = w; k < chunks; k += 8) s += part[(size_t)k * cols + c];
+  ws[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && c < cols) {
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; i++) t += ws[i][lane];
+    out[c] = t;
+  }
+}
+
+// out = the sum of the split-K partial products (fp32)
+__global__ void splitk_sum(const float* __restrict__ part, int splits, size_t stride, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int k = 0; k < splits; k++) v += part[k * stride + i];
+    out[i] = v;
+  }
 }
 
 // dA = (sum of the split-K partial products) * (H > 0), bf16 out
@@ -547,8 +568,9 @@ struct hp_mlp {
   // fused top-k: per row up to 16 candidates of each of up to 2 lists per 256-class tile
   float* cand_v = nullptr;
   int32_t* cand_i = nullptr;
-  // column-sum partials (max_batch / 256 + 1 chunks x the widest layer) and split-K partial
-  // products of the output layer's input gradient (kSplitK x max_batch x H2)
+  // column-sum partials (max_batch / 32 + 1 chunks x the widest layer: 256-row chunks of the
+  // hidden layers, 32-row blocks of the output layer's gradient) and split-K partial products of
+  // the output layer's input gradient (kSplitK x max_batch x H2)
   float* colws = nullptr;
   float* splitws = nullptr;
   // training with the softmax in the output layer's epilogue: per-list row statistics, the
@@ -560,6 +582,7 @@ struct hp_mlp {
   int32_t* perm = nullptr;
   bf16* w3p = nullptr;
   float* b3p = nullptr;
+  bool w3p_stale = false;  // an optimizer step changed W3 since w3p / b3p were gathered
   int steps = 0;
 };
 
@@ -607,12 +630,60 @@ void transpose(const bf16* in, int ldin, int rows, int cols, bf16* out, int ldou
 
 int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
 
+int sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
 constexpr int kSplitK = 8;
+
+// Slices of a split-K GEMM with `tiles` output tiles and nk K chunks: among 1..kmax, the fewest
+// that minimise the busiest CTA's chunk count ceil(tiles k / SMs) ceil(nk / k) (one CTA per SM).
+int pick_ksplit(int tiles, int nk, int kmax) {
+  const int g = sms();
+  int best = 1;
+  long long best_cost = LLONG_MAX;
+  for (int k = 1; k <= std::min(kmax, nk); k++) {
+    const long long cost = (long long)((tiles * k + g - 1) / g) * ((nk + k - 1) / k);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = k;
+    }
+  }
+  return best;
+}
+
+// tcgen05 path: a weight gradient out [M x N] = dA^T H over the batch (K rows), with dA stored
+// [K][M] (row stride lda) and H stored [K][N] (row stride ldb), both read MN-major.  Few output
+// tiles, so K is split over about one CTA per SM and the slices are summed into out.
+int weight_grad(hp_mlp* m, const bf16* dA, int lda, const bf16* H, int ldb, int M, int N, int K, float* out,
+                cudaStream_t st) {
+  const int tiles = ((M + hp::kTcTileM - 1) / hp::kTcTileM) * ((N + hp::kTcTileN - 1) / hp::kTcTileN);
+  const int nk = (K + 63) / 64;
+  const size_t cap = (size_t)kSplitK * m->max_batch * m->H2;  // splitws floats
+  int ks = std::max(1, std::min(nk, sms() / std::max(tiles, 1)));
+  while (ks > 1 && (size_t)ks * M * N > cap) ks--;
+  hp::TcEpilogue ep;
+  ep.a_mn = ep.b_mn = true;
+  ep.ldcf = N;
+  if (ks == 1) {
+    ep.Cf = out;
+    return hp::tc_gemm(dA, lda, H, ldb, M, N, K, ep, m->tc_err, st);
+  }
+  ep.Cf = m->splitws;
+  ep.ksplit = ks;
+  ep.split_stride = (size_t)M * N;
+  const int rc = hp::tc_gemm(dA, lda, H, ldb, M, N, K, ep, m->tc_err, st);
+  if (rc == HP_OK) splitk_sum<<<grid_for((size_t)M * N), 256, 0, st>>>(m->splitws, ks, ep.split_stride, out, (size_t)M * N);
+  return rc;
+}
 
 void colsum(const bf16* in, int ld, int rows, int cols, float* out, float* ws, cudaStream_t st) {
   const int chunks = (rows + kColChunk - 1) / kColChunk;
   colsum_partial<<<dim3((cols + 255) / 256, chunks), 128, 0, st>>>(in, ld, rows, cols, ws);
-  colsum_final<<<(cols + 255) / 256, 256, 0, st>>>(ws, chunks, cols, out);
+  colsum_final<<<(cols + 31) / 32, 256, 0, st>>>(ws, chunks, cols, out);
 }
 
 // Hidden layers for rows [0, rows) whose ids are in `ids` (n valid) -> m->Hb2
@@ -632,34 +703,26 @@ int forward(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStrea
   return rc;
 }
 
-// Gradients of the mean cross-entropy over the n valid rows into m->g[*]; loss sum into m->loss
-// (with have_dz, the logits' gradient dZ, its transpose dZT and the loss are already there)
-int backward(hp_mlp* m, int n, int rows, cudaStream_t st, bool have_dz = false) {
+// Adam hyper-parameters of one optimizer step (c1, c2: the bias corrections of this step)
+struct AdamStep {
+  float lr, b1, b2, eps, c1, c2;
+};
+
+// mma.sync path (HP_MLP_LEGACY_MMA=1): gradients of the mean cross-entropy over the n valid rows
+// into m->g[*] and the loss sum into m->loss, from the logits in m->Z, with transposed copies of
+// the operands of the weight gradients
+int backward_legacy(hp_mlp* m, int n, int rows, cudaStream_t st) {
   int rc = HP_OK;
   const int S = m->S, H1 = m->H1, H2 = m->H2, Kin = m->Kin, Spad = m->Spad;
-  if (!have_dz) {
-    cudaMemsetAsync(m->loss, 0, sizeof(float), st);
-    softmax_xent<<<rows, 256, 0, st>>>(m->Z, Spad, S, m->labels, m->dZ, Spad, Spad, 1.f / (float)std::max(n, 1), m->loss);
-  }
+  cudaMemsetAsync(m->loss, 0, sizeof(float), st);
+  softmax_xent<<<rows, 256, 0, st>>>(m->Z, Spad, S, m->labels, m->dZ, Spad, Spad, 1.f / (float)std::max(n, 1), m->loss);
   // layer 3
   colsum(m->dZ, Spad, rows, S, m->g[5], m->colws, st);
-  if (!have_dz) transpose(m->dZ, Spad, rows, Spad, m->dZT, rows, rows, st);
+  transpose(m->dZ, Spad, rows, Spad, m->dZT, rows, rows, st);
   transpose(m->Hb2, H2, rows, H2, m->H2T, rows, rows, st);
   if (rc == HP_OK) rc = gemm(m->dZT, rows, m->H2T, rows, S, H2, rows, nullptr, 0, m->g[4], H2, nullptr, 0, st, m->tc_err);
-  if (tc_enabled()) {
-    // rows x H2 output with a Spad-long contraction: too few tiles for the GPU, so split K
-    hp::TcEpilogue ep;
-    ep.Cf = m->splitws;
-    ep.ldcf = H2;
-    ep.ksplit = std::min(kSplitK, (Spad + 63) / 64);
-    ep.split_stride = (size_t)rows * H2;
-    if (rc == HP_OK) rc = hp::tc_gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, ep, m->tc_err, st);
-    splitk_relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->splitws, ep.ksplit, ep.split_stride, m->Hb2,
-                                                                      m->dA2, (size_t)rows * H2);
-  } else {
-    if (rc == HP_OK) rc = gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, nullptr, 0, m->dHf, H2, nullptr, 0, st, m->tc_err);
-    relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->dHf, m->Hb2, m->dA2, (size_t)rows * H2);
-  }
+  if (rc == HP_OK) rc = gemm(m->dZ, Spad, m->w3t, Spad, rows, H2, Spad, nullptr, 0, m->dHf, H2, nullptr, 0, st, m->tc_err);
+  relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->dHf, m->Hb2, m->dA2, (size_t)rows * H2);
   // layer 2
   colsum(m->dA2, H2, rows, H2, m->g[3], m->colws, st);
   transpose(m->dA2, H2, rows, H2, m->dA2T, rows, rows, st);
@@ -675,14 +738,76 @@ int backward(hp_mlp* m, int n, int rows, cudaStream_t st, bool have_dz = false) 
   return rc;
 }
 
+// tcgen05 path, after the output layer's gradient epilogue has written dZ (and the 32-row column
+// sums of dZ into colws): the weight gradients read their operands MN-major (no transposed
+// copies), the input gradients read the weights MN-major.  With adam, W3 gets no gradient
+// buffer: the GEMM that forms its gradient applies the Adam step and writes W3's bf16 copy, after
+// the layer's input gradient has been formed from the old W3.
+int backward_tc(hp_mlp* m, int rows, cudaStream_t st, const AdamStep* adam) {
+  int rc = HP_OK;
+  const int S = m->S, H1 = m->H1, H2 = m->H2, Kin = m->Kin, Spad = m->Spad;
+  // layer 3: b3, then dH2 = dZ W3 (rows x H2 with an S-long contraction: too few tiles for the
+  // GPU, so split K), then W3's gradient dZ^T H2 (stored or applied)
+  colsum_final<<<(S + 31) / 32, 256, 0, st>>>(m->colws, rows / 32, S, m->g[5]);
+  {
+    hp::TcEpilogue ep;
+    ep.b_mn = true;
+    ep.Cf = m->splitws;
+    ep.ldcf = H2;
+    ep.ksplit = pick_ksplit(((rows + hp::kTcTileM - 1) / hp::kTcTileM) * ((H2 + hp::kTcTileN - 1) / hp::kTcTileN),
+                            (S + 63) / 64, kSplitK);
+    ep.split_stride = (size_t)rows * H2;
+    rc = hp::tc_gemm(m->dZ, Spad, m->w3b, H2, rows, H2, S, ep, m->tc_err, st);
+    splitk_relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->splitws, ep.ksplit, ep.split_stride, m->Hb2,
+                                                                      m->dA2, (size_t)rows * H2);
+  }
+  {
+    hp::TcEpilogue ep;
+    ep.a_mn = ep.b_mn = true;
+    ep.ldcf = H2;
+    if (adam) {
+      ep.adam_w = m->w[4];
+      ep.adam_m = m->m[4];
+      ep.adam_v = m->v[4];
+      ep.lr = adam->lr;
+      ep.b1 = adam->b1;
+      ep.b2 = adam->b2;
+      ep.eps = adam->eps;
+      ep.c1 = adam->c1;
+      ep.c2 = adam->c2;
+      ep.Cb = m->w3b;
+      ep.ldcb = H2;
+    } else {
+      ep.Cf = m->g[4];
+    }
+    if (rc == HP_OK) rc = hp::tc_gemm(m->dZ, Spad, m->Hb2, H2, S, H2, rows, ep, m->tc_err, st);
+  }
+  // layer 2
+  colsum(m->dA2, H2, rows, H2, m->g[3], m->colws, st);
+  if (rc == HP_OK) rc = weight_grad(m, m->dA2, H2, m->Hb1, H1, H2, H1, rows, m->g[2], st);
+  {
+    hp::TcEpilogue ep;
+    ep.b_mn = true;
+    ep.Cf = m->dHf;
+    ep.ldcf = H1;
+    if (rc == HP_OK) rc = hp::tc_gemm(m->dA2, H2, m->w2b, H1, rows, H1, H2, ep, m->tc_err, st);
+  }
+  relu_backward<<<grid_for((size_t)rows * H1), 256, 0, st>>>(m->dHf, m->Hb1, m->dA1, (size_t)rows * H1);
+  // layer 1
+  colsum(m->dA1, H1, rows, H1, m->g[1], m->colws, st);
+  if (rc == HP_OK) rc = weight_grad(m, m->dA1, H1, m->X, Kin, H1, Kin, rows, m->g[0], st);
+  return rc;
+}
+
 // Loss and gradients of one batch.  On the tcgen05 path the softmax runs in the output layer's
 // epilogue: a first pass of the layer's GEMM keeps per-row maxima and sums of exponentials, a
-// second pass recomputes the logits and writes their gradient in both layouts, so the fp32 logits
-// never reach memory and no transpose of the gradient is needed.
-int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
+// second pass recomputes the logits and writes their gradient (and its 32-row column sums), so
+// the fp32 logits never reach memory.
+int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st,
+                       const AdamStep* adam = nullptr) {
   if (!tc_enabled()) {
     int rc = forward(m, ids, n, rows, st);
-    if (rc == HP_OK) rc = backward(m, n, rows, st);
+    if (rc == HP_OK) rc = backward_legacy(m, n, rows, st);
     return rc;
   }
   int rc = forward_hidden(m, ids, n, rows, st);
@@ -695,7 +820,7 @@ int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, int n, int rows
   if (rc == HP_OK) rc = hp::tc_gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, ea, m->tc_err, st);
   if (rc != HP_OK) return rc;
   cudaMemsetAsync(m->loss, 0, sizeof(float), st);
-  hp::tc_softmax_finish(m->stats, hp::tc_topk_lists(rows, m->S), rows, m->labels, m->zlab, m->row_m, m->row_inv, m->loss,
+  hp::tc_softmax_finish(m->stats, hp::tc_stats_lists(rows, m->S), rows, m->labels, m->zlab, m->row_m, m->row_inv, m->loss,
                         st);
   hp::TcEpilogue eb;
   eb.kt = -2;
@@ -703,27 +828,40 @@ int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, int n, int rows
   eb.labels = m->labels;
   eb.row_m = m->row_m;
   eb.row_inv = m->row_inv;
+  eb.zlab = m->zlab;
   eb.scale = 1.f / (float)std::max(n, 1);
   eb.dz = m->dZ;
   eb.ldz = m->Spad;
-  eb.dzt = m->dZT;
-  eb.ldzt = rows;
+  eb.colpart = m->colws;
   rc = hp::tc_gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, eb, m->tc_err, st);
-  if (rc == HP_OK) rc = backward(m, n, rows, st, true);
+  if (rc == HP_OK) rc = backward_tc(m, rows, st, adam);
   return rc;
 }
 
-// refresh the bf16 copies and transposes used by the forward and backward GEMMs (cast: also the
-// plain bf16 copies, which the optimizer step writes itself)
+// the output layer's weights and biases in the top-k GEMM's scattered class order
+void gather_w3p(hp_mlp* m, cudaStream_t st) {
+  gather_rows<<<grid_for((size_t)m->S * (m->H2 / 8)), 256, 0, st>>>(m->w3b, m->w[5], m->perm, m->S, m->H2, m->w3p, m->b3p);
+  m->w3p_stale = false;
+}
+
+// refresh the bf16 copies used by the GEMMs (cast: the plain bf16 copies, which the optimizer
+// step writes itself; the mma.sync path also needs the weights' transposes); the scattered copy
+// for the top-k is gathered here when cast is set and otherwise marked stale, for the next top-k
+// call
 void refresh_copies(hp_mlp* m, cudaStream_t st, bool cast = true) {
   if (cast) {
     cast_bf16<<<grid_for(m->n[0]), 256, 0, st>>>(m->w[0], m->w1b, m->n[0]);
     cast_bf16<<<grid_for(m->n[2]), 256, 0, st>>>(m->w[2], m->w2b, m->n[2]);
     cast_bf16<<<grid_for(m->n[4]), 256, 0, st>>>(m->w[4], m->w3b, m->n[4]);
   }
-  transpose(m->w2b, m->H1, m->H2, m->H1, m->w2t, m->H2, m->H2, st);
-  transpose(m->w3b, m->H2, m->S, m->H2, m->w3t, m->Spad, m->Spad, st);
-  gather_rows<<<grid_for((size_t)m->S * (m->H2 / 8)), 256, 0, st>>>(m->w3b, m->w[5], m->perm, m->S, m->H2, m->w3p, m->b3p);
+  if (!tc_enabled()) {
+    transpose(m->w2b, m->H1, m->H2, m->H1, m->w2t, m->H2, m->H2, st);
+    transpose(m->w3b, m->H2, m->S, m->H2, m->w3t, m->Spad, m->Spad, st);
+  }
+  if (cast)
+    gather_w3p(m, st);
+  else
+    m->w3p_stale = true;
 }
 
 void free_model(hp_mlp* m) {
@@ -783,31 +921,34 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
   al(&m->w1b, m->n[0] * 2);
   al(&m->w2b, m->n[2] * 2);
   al(&m->w3b, m->n[4] * 2);
-  al(&m->w2t, (size_t)H1 * H2 * 2);
-  al(&m->w3t, (size_t)H2 * m->Spad * 2);
   al(&m->X, B * m->Kin * 2);
-  al(&m->XT, (size_t)m->Kin * B * 2);
   al(&m->Hb1, B * H1 * 2);
   al(&m->Hb2, B * H2 * 2);
-  al(&m->H1T, (size_t)H1 * B * 2);
-  al(&m->H2T, (size_t)H2 * B * 2);
   al(&m->Z, B * m->Spad * 4);
   al(&m->dHf, B * std::max(H1, H2) * 4);
   al(&m->loss, 4);
   al(&m->dZ, B * m->Spad * 2);
-  al(&m->dZT, (size_t)m->Spad * B * 2);
   al(&m->dA2, B * H2 * 2);
-  al(&m->dA2T, (size_t)H2 * B * 2);
   al(&m->dA1, B * H1 * 2);
-  al(&m->dA1T, (size_t)H1 * B * 2);
+  if (!tc_enabled()) {
+    // the mma.sync path's transposed copies (the tcgen05 GEMMs read these operands MN-major)
+    al(&m->w2t, (size_t)H1 * H2 * 2);
+    al(&m->w3t, (size_t)H2 * m->Spad * 2);
+    al(&m->XT, (size_t)m->Kin * B * 2);
+    al(&m->H1T, (size_t)H1 * B * 2);
+    al(&m->H2T, (size_t)H2 * B * 2);
+    al(&m->dZT, (size_t)m->Spad * B * 2);
+    al(&m->dA2T, (size_t)H2 * B * 2);
+    al(&m->dA1T, (size_t)H1 * B * 2);
+  }
   al(&m->labels, B * 4);
   al(&m->tc_err, sizeof(unsigned));
   const size_t ncand = (size_t)max_batch * ((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcListsPerTile * 16;
   al(&m->cand_v, ncand * 4);
   al(&m->cand_i, ncand * 4);
-  al(&m->colws, (size_t)(B / kColChunk + 1) * std::max(m->Spad, std::max(H1, H2)) * 4);
+  al(&m->colws, (size_t)(B / 32 + 1) * std::max(m->Spad, std::max(H1, H2)) * 4);
   al(&m->splitws, (size_t)kSplitK * B * H2 * 4);
-  al(&m->stats, (size_t)((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcListsPerTile * B * 2 * 4);
+  al(&m->stats, (size_t)((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcStatsListsPerTile * B * 2 * 4);
   al(&m->zlab, B * 4);
   al(&m->row_m, B * 4);
   al(&m->row_inv, B * 4);
@@ -912,16 +1053,20 @@ extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t
   const int rows = round_up(n, 32);
   cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
   cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
-  if (rc != HP_OK) return rc;
-  m->steps++;
+  const int step = m->steps + 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float c1 = 1.f / (1.f - powf(b1, (float)m->steps)), c2 = 1.f / (1.f - powf(b2, (float)m->steps));
+  const AdamStep adam{lr, b1, b2, eps, 1.f / (1.f - powf(b1, (float)step)), 1.f / (1.f - powf(b2, (float)step))};
+  // on the tcgen05 path W3's update is fused into the GEMM that forms its gradient
+  const bool fused = tc_enabled();
+  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st, fused ? &adam : nullptr);
+  if (rc != HP_OK) return rc;
+  m->steps = step;
   // the weight matrices' bf16 copies are written by the update itself
   bf16* const wb[6] = {m->w1b, nullptr, m->w2b, nullptr, m->w3b, nullptr};
   for (int i = 0; i < 6; i++)
-    adam_update<<<grid_for(m->n[i]), 256, 0, st>>>(m->w[i], m->g[i], m->m[i], m->v[i], wb[i], m->n[i], lr, b1, b2, eps,
-                                                     c1, c2);
+    if (!(fused && i == 4))
+      adam_update<<<grid_for(m->n[i]), 256, 0, st>>>(m->w[i], m->g[i], m->m[i], m->v[i], wb[i], m->n[i], adam.lr, adam.b1,
+                                                       adam.b2, adam.eps, adam.c1, adam.c2);
   refresh_copies(m, st, false);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_train_step: launch");
@@ -940,6 +1085,7 @@ extern "C" int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t 
   if (!m || !d_ids || !d_top) return hp::fail(HP_EINVAL, "hp_mlp_topk: NULL argument");
   if (k < 1 || k > kTopKMax || k > m->S) return hp::fail(HP_EINVAL, "hp_mlp_topk: k must be in [1, 16] and <= S");
   cudaStream_t st = (cudaStream_t)stream;
+  if (tc_enabled() && m->w3p_stale) gather_w3p(m, st);
   for (int64_t off = 0; off < n; off += m->max_batch) {
     const int nb = (int)std::min<int64_t>(m->max_batch, n - off);
     const int rows = round_up(nb, 32);

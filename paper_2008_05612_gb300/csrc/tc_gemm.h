@@ -1,5 +1,7 @@
-// The tcgen05 GEMM: C = A B^T for bf16 A [M x K] and B [N x K] (both K-major, row strides a
-// multiple of 8 elements, 16-byte aligned bases), fp32 accumulation in tensor memory.
+// The tcgen05 GEMM: C = A B^T for bf16 A [M x K] and B [N x K], fp32 accumulation in tensor
+// memory.  Each operand is K-major (A stored [M][K], B [N][K]) or, with a_mn / b_mn, MN-major
+// (A stored [K][M], B [K][N], i.e. the GEMM reads the transpose of a row-major matrix); row
+// strides a multiple of 8 elements, 16-byte aligned bases.
 // Either the tile is stored (fp32 and / or bf16, after an optional bias per column and ReLU) or,
 // in top-k mode, each row keeps only its kt best (bias-added) columns per 256-column tile.
 #pragma once
@@ -12,9 +14,11 @@
 namespace hp {
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
-constexpr int kTcListsPerTile = 2;  // top-k mode: candidate lists per row and 256-column tile range
+constexpr int kTcListsPerTile = 2;       // top-k mode: candidate lists per row and 256-column tile range
+constexpr int kTcStatsListsPerTile = 4;  // row-statistics mode: lists per row and tile range
 
 struct TcEpilogue {
+  bool a_mn = false, b_mn = false;  // operand layouts (see above)
   const float* bias = nullptr;  // [N] added to every row, or null
   int relu = 0;
   float* Cf = nullptr;  // fp32 output [M x ldcf] or null
@@ -33,12 +37,17 @@ struct TcEpilogue {
   const int32_t* col_id = nullptr;
   // softmax modes over the columns of each row (the proposal's training step; bias added, rows
   // with label -1 ignored):
-  //   kt = -1 (row statistics): per row and column list l (as in top-k mode) the running
-  //     maximum m and sum of exp(x - m) go to stats[2 (l M + r) + {0, 1}]; the logit at the row's
-  //     label goes to zlab[r];
-  //   kt = -2 (cross-entropy gradient): with row_m / row_inv the row's maximum and 1 / sum,
+  //   kt = -1 (row statistics): the columns are split into L = tc_stats_lists(M, N) disjoint
+  //     sets (unions of 64-column slices of the tiles); per row r and set l the running maximum m
+  //     and sum of exp(x - m) go to stats[2 (l M + r) + {0, 1}]; the logit at the row's label goes
+  //     to zlab[r];
+  //   kt = -2 (cross-entropy gradient): with row_m / row_inv the row's maximum and 1 / sum and
+  //     zlab the label logits of the statistics pass,
   //     dz = (exp(x - m) / sum - [column == label]) * scale, zero for label -1, stored as bf16 both
-  //     row-major (dz, row stride ldz) and transposed (dzt, row stride ldzt)
+  //     row-major (dz, row stride ldz >= N, a multiple of 8; base 16-byte aligned; it leaves
+  //     through TMA stores, columns >= N and rows >= M are not written); if colpart is set,
+  //     colpart[b * N + c] = the sum over the rows
+  //     32 b .. 32 b + 31 of the stored (bf16) dz[row, c], in a fixed order
   const int32_t* labels = nullptr;
   float* stats = nullptr;
   float* zlab = nullptr;
@@ -47,8 +56,18 @@ struct TcEpilogue {
   float scale = 1.f;
   __nv_bfloat16* dz = nullptr;
   int ldz = 0;
-  __nv_bfloat16* dzt = nullptr;
-  int ldzt = 0;
+  float* colpart = nullptr;
+  // store mode with an Adam step in place of the fp32 store (no bias, ReLU or split-K): the tile
+  // is the gradient g of the fp32 weights adam_w [M x ldcf] with moments adam_m, adam_v (same
+  // layout); per element m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+  // w -= lr (m c1) / (sqrt(v c2) + eps); the new w also goes to Cb (bf16) and, if set, transposed
+  // to wt (bf16, wt[c * ldwt + r])
+  float* adam_w = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float lr = 0.f, b1 = 0.f, b2 = 0.f, eps = 0.f, c1 = 0.f, c2 = 0.f;
+  __nv_bfloat16* wt = nullptr;
+  int ldwt = 0;
   // split-K (store mode, fp32 output only, no bias / ReLU): the K chunks are cut into ksplit
   // contiguous slices computed by different CTAs; slice j's partial product goes to
   // Cf + j * split_stride, and the caller sums the slices
@@ -63,6 +82,9 @@ int tc_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, in
 
 // Number of candidate lists per row that top-k mode writes (at most 2 ceil(N / 256)).
 int tc_topk_lists(int M, int N);
+
+// Number of statistics lists per row that row-statistics mode writes (at most 4 ceil(N / 256)).
+int tc_stats_lists(int M, int N);
 
 // Combine the row-statistics lists of kt = -1 mode: row_m[r], row_inv[r] = 1 / sum, and for
 // labelled rows log(sum) + m - zlab[r] added to *loss.

@@ -188,3 +188,43 @@ def test_host_or_strided_ids_are_refused(hp):
         net.logits(torch.zeros(8, dtype=torch.int64, device="cuda")[::2])
     with pytest.raises(TypeError):
         net.train_step(torch.zeros(4, dtype=torch.int64), torch.zeros(4, dtype=torch.int32, device="cuda"), 1e-3)
+
+
+@pytest.mark.parametrize("N,H1,H2,S,n", [(27, 64, 96, 1000, 250), (27, 512, 512, 8200, 512)])
+def test_train_step_is_one_adam_step_on_the_gradients(hp, N, H1, H2, S, n):
+    """The training step (its output layer's update fused into the GEMM that forms the layer's weight
+    gradient, which also writes the weights' bf16 copy and its transpose) equals one plain Adam step
+    (Kingma & Ba, first step from zero moments) on the gradients of the same batch: a second network
+    built from the updated parameters gives the same logits and the same next gradients."""
+    p = init(N, H1, H2, S, 51)
+    A = hp.MLP(N, H1, H2, S, 512, p)
+    ids = inputs.sample_ids(N, n, seed=12)
+    labels = (inputs.splitmix64(ids) % np.uint64(S)).astype(np.int32)
+    ids_t, lab_t = ids_tensor(ids), torch.from_numpy(labels).cuda()
+    probe = ids_tensor(inputs.sample_ids(N, 300, seed=13))
+    z0 = A.logits(probe).cpu().numpy().astype(np.float64)
+    _, g = A.gradients(ids_t, lab_t)
+    lr, b1, b2, eps = np.float32(1e-3), np.float32(0.9), np.float32(0.999), np.float32(1e-8)
+    c1, c2 = np.float32(1) / (np.float32(1) - b1), np.float32(1) / (np.float32(1) - b2)
+    p1 = []
+    for w, gi in zip(p, g):
+        w, gi = np.asarray(w, np.float32), np.asarray(gi, np.float32)
+        m = (np.float32(1) - b1) * gi
+        v = (np.float32(1) - b2) * gi * gi
+        p1.append((w - lr * (m * c1) / (np.sqrt(v * c2) + eps)).astype(np.float32))
+    A.train_step(ids_t, lab_t, float(lr))
+    A.status()
+    B = hp.MLP(N, H1, H2, S, 512, p1)
+    zA = A.logits(probe).cpu().numpy().astype(np.float64)
+    zB = B.logits(probe).cpu().numpy().astype(np.float64)
+    moved = rel(zA, z0)
+    print("logit change of the step %.4f, fused vs plain %.2e" % (moved, rel(zA, zB)))
+    assert moved > 1e-3
+    assert rel(zA, zB) < min(5e-3, 0.1 * moved)
+    ids2 = inputs.sample_ids(N, n, seed=14)
+    lab2 = torch.from_numpy((inputs.splitmix64(ids2) % np.uint64(S)).astype(np.int32)).cuda()
+    lA, gA = A.gradients(ids_tensor(ids2), lab2)
+    lB, gB = B.gradients(ids_tensor(ids2), lab2)
+    assert abs(lA - lB) < 1e-3 * abs(lB)
+    for a, b in zip(gA, gB):
+        assert rel(a.astype(np.float64), b.astype(np.float64)) < 1e-2
