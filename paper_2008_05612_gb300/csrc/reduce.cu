@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "hp_internal.h"
 
@@ -16,8 +17,10 @@ namespace {
 constexpr unsigned kErrRange = 4u;     // a map entry outside [-1, S)
 constexpr unsigned kErrUnion = 8u;     // union retries exhausted
 constexpr int kHistThreads = 1024;
-constexpr int kRobTileBits = 14;       // 2^14 ids (64 KB) of the map per CTA
+constexpr int kRobTileBits = 13;       // 2^13 ids (32 KB) of the map per block, two blocks per CTA
+constexpr int kRobMaxPassBits = 8;     // high bits per later pass (a block keeps >= 32 contiguous ids)
 constexpr int kRobThreads = 512;
+constexpr int kRobReplicas = 16;       // copies of each phenotype's two counters (spreads hot-phenotype atomics)
 
 // ---------------------------------------------------------------- designability
 
@@ -108,50 +111,170 @@ __global__ void hist_global(const int32_t* __restrict__ phen, unsigned long long
 
 // ---------------------------------------------------------------- robustness
 
-// One CTA per tile of 2^kRobTileBits consecutive ids: flips of the low bits are
-// read from shared memory, flips of higher bits from global memory.  Only
-// genotypes with P(g) >= 0 examine their flips; the -1 row follows from the
-// edge identity sum_{P(g)=-1} #{i: P(g^2^i) = -1} = N N_{-1} - sum_{p>=0} to_del[p].
-__global__ void __launch_bounds__(kRobThreads) robustness_tiles(const int32_t* __restrict__ phen, int N, int S,
-                                                                unsigned long long* __restrict__ neutral,
-                                                                unsigned long long* __restrict__ to_del,
-                                                                unsigned long long* __restrict__ negcount,
-                                                                unsigned* __restrict__ err) {
-  extern __shared__ int32_t tile[];
-  const int k = min(N, kRobTileBits);
-  const unsigned long long tsize = 1ull << k;
-  const unsigned long long g0 = (unsigned long long)blockIdx.x << k;
-  for (unsigned long long j = threadIdx.x; j < tsize; j += blockDim.x) tile[j] = __ldcs(phen + g0 + j);
-  __syncthreads();
-  unsigned neg = 0;
-  for (unsigned long long j = threadIdx.x; j < tsize; j += blockDim.x) {
-    const int32_t p = tile[j];
-    if (p < 0) {
-      neg += p == -1;
-      if (p != -1) atomicOr(err, kErrRange);
-      continue;
-    }
-    if (p >= S) {
-      atomicOr(err, kErrRange);
-      continue;
-    }
-    unsigned nn = 0, nd = 0;
-    for (int i = 0; i < k; i++) {
-      const int32_t q = tile[j ^ (1ull << i)];
-      nn += q == p;
-      nd += q < 0;
-    }
-    const unsigned long long g = g0 + j;
-    for (int i = k; i < N; i++) {
-      const int32_t q = __ldg(phen + (g ^ (1ull << i)));
-      nn += q == p;
-      nd += q < 0;
-    }
-    if (nn) atomicAdd(&neutral[p], (unsigned long long)nn);
-    if (nd) atomicAdd(&to_del[p], (unsigned long long)nd);
+// Eq. 2 numerators in passes over the map, each reading it once.  A block is 2^kRobTileBits ids
+// in shared memory: 2^c consecutive ids times every combination of the pass's h bits
+// (c + h = kRobTileBits), the other bits of the id fixed by the block index.  The first pass
+// takes 2^13 consecutive ids and counts the flips of bits 0..12; each later pass counts the flips
+// of its own h bits, so every flip of every genotype is counted once, from shared memory, with
+// the map read 1 + ceil((N - 13) / 8) times instead of once per high bit.  Only genotypes with
+// P(g) >= 0 examine their flips; the -1 row follows from the edge identity
+// sum_{P(g)=-1} #{i: P(g^2^i) = -1} = N N_{-1} - sum_{p>=0} to_del[p].
+// A CTA walks blocks with the next block's asynchronous copy in flight; the block's genotypes
+// that fold are listed first, then examined one per lane.  The counts go to replica blockIdx % R of each phenotype's counters
+// (neutral[r S + p], to_del[r S + p]), so that the atomics of a very designable phenotype are
+// spread over R addresses; robustness_gather adds the replicas up.
+struct RobPass {
+  int c, h;                   // contiguous low bits of a block; pass bits
+  int pos[kRobMaxPassBits];   // positions of the pass bits (all >= c)
+  int nrest;                  // the remaining id bits, filled from the block index (low bit first)
+  int rest[64];
+  int first;                  // first pass: counts the contiguous bits' flips, checks ranges, counts -1
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kRobThreads) robustness_pass(const int32_t* __restrict__ phen, int S, const RobPass P,
+                                                               unsigned long long nblocks, int replicas,
+                                                               unsigned long long* __restrict__ neutral_rep,
+                                                               unsigned long long* __restrict__ to_del_rep,
+                                                               unsigned long long* __restrict__ negcount,
+                                                               unsigned* __restrict__ err) {
+  extern __shared__ int32_t tiles[];  // two blocks, then the list of a block's genotypes that fold
+  __shared__ unsigned long long hoff[1 << kRobMaxPassBits];
+  __shared__ unsigned nlist;
+  constexpr int kIds = 1 << kRobTileBits;
+  uint16_t* list = reinterpret_cast<uint16_t*>(tiles + 2 * kIds);
+  static_assert(kRobTileBits <= 16, "list entries are 16-bit local indices");
+  for (int i = threadIdx.x; i < (1 << P.h); i += blockDim.x) {
+    unsigned long long off = 0;
+    for (int t = 0; t < P.h; t++)
+      if ((i >> t) & 1) off |= 1ull << P.pos[t];
+    hoff[i] = off;
   }
-  for (int off = 16; off; off >>= 1) neg += __shfl_xor_sync(0xFFFFFFFFu, neg, off);
-  if ((threadIdx.x & 31) == 0 && neg) atomicAdd(negcount, (unsigned long long)neg);
+  __syncthreads();
+  const int c = P.c;
+  const unsigned cmask = (1u << c) - 1u, ids = 1u << (c + P.h);  // ids < kIds only when N < kRobTileBits
+  const bool vec = reinterpret_cast<uintptr_t>(phen) % 16 == 0 && c >= 2 && ids == (unsigned)kIds;
+  auto block_base = [&](unsigned long long b) {
+    unsigned long long base = 0;
+    for (int t = 0; t < P.nrest; t++)
+      if ((b >> t) & 1ull) base |= 1ull << P.rest[t];
+    return base;
+  };
+  // block b into slot: 16-byte asynchronous copies (four ids never straddle two runs when c >= 2)
+  constexpr int kLoads = kIds / (4 * kRobThreads);
+  auto issue = [&](unsigned long long b, int slot) {
+    const unsigned long long base = block_base(b);
+    int32_t* t = tiles + slot * kIds;
+#pragma unroll
+    for (int k = 0; k < kLoads; k++) {
+      const unsigned j = 4 * (threadIdx.x + k * kRobThreads);
+      cp_async16(t + j, phen + base + hoff[j >> c] + (j & cmask));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // counted flips: local bits 0..c-1 in the first pass, c..c+h-1 in the others
+  const int nbits = P.first ? c : P.h, bit0 = P.first ? 0 : c;
+  const int lane = threadIdx.x & 31;
+  unsigned long long* __restrict__ neutral = neutral_rep + (size_t)(blockIdx.x % replicas) * S;
+  unsigned long long* __restrict__ to_del = to_del_rep + (size_t)(blockIdx.x % replicas) * S;
+  unsigned neg = 0;
+  unsigned long long b = blockIdx.x;
+  if (vec && b < nblocks) issue(b, 0);
+  for (int it = 0; b < nblocks; b += gridDim.x, it++) {
+    int32_t* tile = tiles + (it & 1) * kIds;
+    if (threadIdx.x == 0) nlist = 0;  // ordered before phase 1 by the barrier after the load
+    const unsigned long long nb = b + gridDim.x;
+    if (vec) {
+      if (nb < nblocks) {
+        issue(nb, (it + 1) & 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+    } else {
+      const unsigned long long base = block_base(b);
+      for (unsigned j = threadIdx.x; j < ids; j += blockDim.x) tile[j] = __ldcs(phen + base + hoff[j >> c] + (j & cmask));
+    }
+    __syncthreads();
+    // phase 1: the block's genotypes that fold, listed (local indices) in shared memory; whole
+    // warps, four ids per lane (one 16-byte read), branch-free; the first pass also counts -1 and
+    // checks the ranges
+    for (unsigned j0 = 4 * (threadIdx.x - lane); j0 < ids; j0 += 4 * blockDim.x) {
+      const unsigned j = j0 + 4 * lane;
+      int4 v4 = make_int4(-1, -1, -1, -1);
+      if (j + 3 < ids) {
+        v4 = *reinterpret_cast<const int4*>(tile + j);
+      } else if (j < ids) {  // blocks of fewer than four ids (maps of N < 2)
+        v4.x = tile[j];
+        if (j + 1 < ids) v4.y = tile[j + 1];
+        if (j + 2 < ids) v4.z = tile[j + 2];
+      }
+      const int32_t e[4] = {v4.x, v4.y, v4.z, v4.w};
+      unsigned flags = 0;
+#pragma unroll
+      for (int k = 0; k < 4; k++) flags |= (unsigned)((unsigned)e[k] < (unsigned)S) << k;
+      if (P.first) {
+        const unsigned valid = j < ids ? min(4u, ids - j) : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          neg += (unsigned)(k < (int)valid && e[k] == -1);
+          if (k < (int)valid && (e[k] < -1 || e[k] >= S)) atomicOr(err, kErrRange);
+        }
+      }
+      // this lane's place in the list: the folding ids of the lanes below it (cnt <= 4, three bits)
+      const unsigned cnt = __popc(flags);
+      const uint32_t lt = (1u << lane) - 1u;
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, cnt & 1u), b1 = __ballot_sync(0xFFFFFFFFu, cnt & 2u),
+                     b2 = __ballot_sync(0xFFFFFFFFu, cnt & 4u);
+      const unsigned below = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+      const unsigned tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+      unsigned at = 0;
+      if (lane == 0 && tot) at = atomicAdd(&nlist, tot);
+      at = __shfl_sync(0xFFFFFFFFu, at, 0) + below;
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (flags & (1u << k)) list[at++] = (uint16_t)(j + k);
+    }
+    __syncthreads();
+    // phase 2: one listed genotype per lane, its counted flips in turn
+    {
+      const unsigned n = nlist;
+      for (unsigned f = threadIdx.x; f < n; f += blockDim.x) {
+        const unsigned idx = list[f];
+        const int32_t p = tile[idx];
+        unsigned nn = 0, nd = 0;
+        for (int t = 0; t < nbits; t++) {
+          const int32_t q = tile[idx ^ (1u << (bit0 + t))];
+          nn += q == p;
+          nd += q < 0;
+        }
+        if (nn) atomicAdd(&neutral[p], (unsigned long long)nn);
+        if (nd) atomicAdd(&to_del[p], (unsigned long long)nd);
+      }
+    }
+    __syncthreads();  // the slot is refilled by the copy issued in the next iteration but one
+  }
+  if (P.first) {
+    for (int off = 16; off; off >>= 1) neg += __shfl_xor_sync(0xFFFFFFFFu, neg, off);
+    if (lane == 0 && neg) atomicAdd(negcount, (unsigned long long)neg);
+  }
+}
+
+__global__ void robustness_gather(const unsigned long long* __restrict__ rep, int replicas, int S,
+                                  unsigned long long* __restrict__ neutral, unsigned long long* __restrict__ to_del) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= S) return;
+  unsigned long long a = 0, d = 0;
+  for (int r = 0; r < replicas; r++) {
+    a += rep[(size_t)r * S + p];
+    d += rep[(size_t)(replicas + r) * S + p];
+  }
+  neutral[p] = a;
+  to_del[p] = d;
 }
 
 __global__ void robustness_finish(int N, int S, unsigned long long* __restrict__ neutral,
@@ -331,11 +454,54 @@ namespace hp {
 cudaError_t launch_robustness(const int32_t* d_phen, int N, int S, unsigned long long* neutral,
                               unsigned long long* to_del, unsigned long long* negcount, unsigned* err, cudaStream_t st) {
   const int k = std::min((int)N, kRobTileBits);
-  const unsigned long long tiles = 1ull << (N - k);
-  const size_t smem = sizeof(int32_t) << k;
-  cudaError_t e = cudaFuncSetAttribute(robustness_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const unsigned long long blocks = 1ull << (N - k);
+  const size_t smem = 2 * (sizeof(int32_t) << kRobTileBits) + (sizeof(uint16_t) << kRobTileBits);
+  cudaError_t e = cudaFuncSetAttribute(robustness_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  robustness_tiles<<<(unsigned)tiles, kRobThreads, smem, st>>>(d_phen, N, S, neutral, to_del, negcount, err);
+  // the passes: bits [0, k) first, then the high bits [k, N) in near-equal groups of at most
+  // kRobMaxPassBits, each with the kRobTileBits - h lowest bits contiguous
+  std::vector<RobPass> plan;
+  {
+    RobPass p{};
+    p.c = k;
+    p.h = 0;
+    p.first = 1;
+    for (int b = k; b < N; b++) p.rest[p.nrest++] = b;
+    plan.push_back(p);
+  }
+  const int R = N - k;
+  const int np = (R + kRobMaxPassBits - 1) / kRobMaxPassBits;
+  for (int i = 0, lo = k; i < np; i++) {
+    RobPass p{};
+    p.h = R / np + (i < R % np ? 1 : 0);
+    p.c = kRobTileBits - p.h;
+    for (int t = 0; t < p.h; t++) p.pos[t] = lo + t;
+    for (int b = p.c; b < N; b++)
+      if (b < lo || b >= lo + p.h) p.rest[p.nrest++] = b;
+    lo += p.h;
+    plan.push_back(p);
+  }
+  // a few CTAs per SM walking the blocks (shared memory: two blocks each), counting into
+  // replicated counters (stream-ordered scratch; without it, straight into neutral / to_del)
+  const unsigned grid = (unsigned)std::min<unsigned long long>(blocks, (unsigned long long)sm_count() * 2);
+  unsigned long long* rep = nullptr;
+  const size_t rep_bytes = sizeof(unsigned long long) * 2 * kRobReplicas * (size_t)S;
+  if (cudaMallocAsync(&rep, rep_bytes, st) != cudaSuccess || cudaMemsetAsync(rep, 0, rep_bytes, st) != cudaSuccess) {
+    if (rep) cudaFreeAsync(rep, st);
+    rep = nullptr;
+    cudaGetLastError();  // clear the failed allocation's error
+  }
+  for (const RobPass& p : plan) {
+    if (rep)
+      robustness_pass<<<grid, kRobThreads, smem, st>>>(d_phen, S, p, blocks, kRobReplicas, rep, rep + (size_t)kRobReplicas * S,
+                                                       negcount, err);
+    else
+      robustness_pass<<<grid, kRobThreads, smem, st>>>(d_phen, S, p, blocks, 1, neutral, to_del, negcount, err);
+  }
+  if (rep) {
+    robustness_gather<<<(S + 255) / 256, 256, 0, st>>>(rep, kRobReplicas, S, neutral, to_del);
+    cudaFreeAsync(rep, st);
+  }
   robustness_finish<<<1, 1024, 0, st>>>(N, S, neutral, to_del, negcount);
   return cudaGetLastError();
 }
