@@ -28,11 +28,12 @@ struct DevTables {
   // per-sequence scan tables (built on first use): conformations sorted by their contact-count
   // vectors; a group is a run of equal vectors (equal A for every sequence)
   uint32_t* scan_gcnt = nullptr;   // 6 x gpad: per group the six count bit-planes, word-major
+  uint32_t* scan_ccnt = nullptr;   // 6 x cpad: per cluster of 32 groups the planes of the maxima
   int32_t* scan_gbeg = nullptr;    // ngroups + 1: first member of each group (scan order)
   uint32_t* scan_mcnt = nullptr;   // 6 x spad: per member its count bit-planes, word-major
   uint32_t* scan_mmask = nullptr;  // NE x spad: per member its contact masks, word-major
   int32_t* scan_midx = nullptr;    // spad: original conformation index of each member
-  int scan_ngroups = 0, scan_gpad = 0, scan_spad = 0;
+  int scan_ngroups = 0, scan_gpad = 0, scan_spad = 0, scan_cpad = 0;
   // class -> first conformation index and number of conformations (built on first use)
   int32_t* class_first = nullptr;
   int32_t* class_nconf = nullptr;

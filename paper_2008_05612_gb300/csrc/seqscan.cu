@@ -51,6 +51,7 @@ constexpr int kScanWarps = 8;  // warps (sequences in flight) per CTA
 
 struct ScanParams {
   const uint32_t* gcnt;      // 6 x gpad count planes per group (even bits 0..2, odd bits 0..2)
+  const uint32_t* ccnt;      // 6 x cpad count planes per cluster of 32 groups (componentwise maxima)
   const int32_t* gbeg;       // ngroups + 1 member ranges
   const uint32_t* mcnt;      // 6 x spad count planes per member (the unpruned scan)
   const uint32_t* mmask;     // NE x spad contact masks per member
@@ -64,7 +65,7 @@ struct ScanParams {
   int32_t* gap;              // n energy gaps E2 - E1 or NULL (GAP variant)
   unsigned long long* counters;  // [0] conformations evaluated exactly, [1] group bounds evaluated
   long long n;
-  int k, rec_words, NE, C, S_dir, ngroups, gpad, spad, prune;
+  int k, rec_words, NE, C, S_dir, ngroups, gpad, spad, prune, nclusters, cpad;
   int T;                     // energy-gap threshold (1 unless GAP)
 };
 
@@ -162,8 +163,8 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
           if (orig[u] >= 0) take(10 * A[u] + 3 * B[u], orig[u]);
       }
     }
-    // the next 32 groups' count planes and member ranges are loaded while the current ones are
-    // tested (the step is short and latency-bound otherwise)
+    // the next surviving cluster's count planes and member ranges are loaded while the current
+    // ones are tested (the step is short and latency-bound otherwise)
     uint32_t cw[6] = {0, 0, 0, 0, 0, 0};
     int cb0 = 0, cb1 = 0;
     auto fetch = [&](int g0, uint32_t (&c)[6], int& b0, int& b1) {
@@ -175,11 +176,41 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
         b1 = __ldg(p.gbeg + gi + 1);
       }
     };
-    if (cand >= 0) fetch(0, cw, cb0, cb1);
-    for (int g0 = 0; cand >= 0 && g0 < p.ngroups; g0 += 32) {
+    // Groups come in clusters of 32 (one warp step): a cluster's componentwise-maximal count
+    // vector has A no smaller than any of its groups' (h >= 0), so when its bound falls below
+    // cut the whole cluster is skipped.  The lanes test 32 clusters at once; next_cluster walks
+    // the survivors.
+    int k0 = -32;
+    uint32_t sv = 0;
+    auto next_cluster = [&]() -> int {
+      while (sv == 0) {
+        k0 += 32;
+        if (k0 >= p.nclusters) return -1;
+        const int ki = k0 + lane;
+        bool keep = false;
+        if (ki < p.nclusters) {
+          uint32_t c[6];
+#pragma unroll
+          for (int k = 0; k < 6; k++) c[k] = __ldg(p.ccnt + (size_t)k * p.cpad + ki);
+          const int A = (__popc(e & c[0]) + __popc(o & c[3])) + 2 * (__popc(e & c[1]) + __popc(o & c[4])) +
+                        4 * (__popc(e & c[2]) + __popc(o & c[5]));
+          n_bound++;
+          keep = upper(A, p.C) >= cut;
+        }
+        sv = __ballot_sync(0xFFFFFFFFu, keep);
+      }
+      const int cl = k0 + __ffs(sv) - 1;
+      sv &= sv - 1;
+      return cl;
+    };
+    int cl = cand >= 0 ? next_cluster() : -1;
+    if (cl >= 0) fetch(cl * 32, cw, cb0, cb1);
+    while (cl >= 0) {
+      const int g0 = cl * 32;
+      cl = next_cluster();
       uint32_t nw[6] = {0, 0, 0, 0, 0, 0};
       int nb0 = 0, nb1 = 0;
-      if (g0 + 32 < p.ngroups) fetch(g0 + 32, nw, nb0, nb1);
+      if (cl >= 0) fetch(cl * 32, nw, nb0, nb1);
       // lane l: group g0 + l, its A and bound
       const int gi = g0 + lane;
       int A = 0, n = 0;
@@ -266,7 +297,10 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
 namespace hp {
 
 // Scan order: conformations sorted by their vector of per-residue contact
-// counts (lexicographic, stable), so equal vectors form contiguous groups.
+// counts, so equal vectors form contiguous groups.  The order interleaves the
+// counts' bits (the high bit of every residue's count, then the middle bits,
+// then the low bits), so that the 32 groups of a cluster have similar counts in
+// every residue and the cluster's componentwise maximum stays tight.
 int scan_tables(const hp_structs* cs, DevTables** out) {
   DevTables* dt = nullptr;
   int rc = device_tables(cs, &dt);
@@ -284,15 +318,30 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
       cvec[c][s->contacts[((size_t)c * s->C + k) * 2]]++;
       cvec[c][s->contacts[((size_t)c * s->C + k) * 2 + 1]]++;
     }
+  std::vector<std::vector<uint8_t>> key((size_t)s->S_dir, std::vector<uint8_t>(3 * (size_t)N, 0));
+  for (int32_t c = 0; c < s->S_dir; c++)
+    for (int b = 2; b >= 0; b--)
+      for (int i = 0; i < N; i++) key[c][(size_t)(2 - b) * N + i] = (cvec[c][i] >> b) & 1;
   std::vector<int32_t> order((size_t)s->S_dir);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cvec[a] < cvec[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
   std::vector<int32_t> gbeg;
   for (size_t j = 0; j < order.size(); j++)
     if (j == 0 || cvec[order[j]] != cvec[order[j - 1]]) gbeg.push_back((int32_t)j);
   const int ngroups = (int)gbeg.size();
   gbeg.push_back((int32_t)order.size());
   const int gpad = (ngroups + 31) / 32 * 32, spad = (s->S_dir + 31) / 32 * 32;
+  const int nclusters = (ngroups + 31) / 32, cpad = (nclusters + 31) / 32 * 32;
+  std::vector<uint32_t> ccnt((size_t)6 * cpad, 0u);
+  for (int cl = 0; cl < nclusters; cl++) {
+    std::vector<uint8_t> mx(N, 0);
+    for (int gi = 32 * cl; gi < std::min(ngroups, 32 * cl + 32); gi++)
+      for (int i = 0; i < N; i++) mx[i] = std::max(mx[i], cvec[order[gbeg[gi]]][i]);
+    // even residue 2k -> bit k of the even planes, odd residue 2k + 1 -> bit k of the odd planes
+    for (int i = 0; i < N; i++)
+      for (int b = 0; b < 3; b++)
+        if ((mx[i] >> b) & 1) ccnt[(size_t)((i & 1) ? 3 + b : b) * cpad + cl] |= 1u << (i >> 1);
+  }
   std::vector<uint32_t> gcnt((size_t)6 * gpad, 0u), mcnt((size_t)6 * spad, 0u), mmask((size_t)std::max(NE, 1) * spad, 0u);
   std::vector<int32_t> midx(spad, -1);
   for (int gi = 0; gi < ngroups; gi++) {
@@ -312,6 +361,8 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
     midx[j] = order[j];
   }
   cudaError_t e = cudaMalloc(&dt->scan_gcnt, gcnt.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_ccnt, ccnt.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_ccnt, ccnt.data(), ccnt.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&dt->scan_gbeg, gbeg.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&dt->scan_mcnt, mcnt.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&dt->scan_mmask, mmask.size() * 4);
@@ -323,12 +374,14 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
   if (e == cudaSuccess) e = cudaMemcpy(dt->scan_midx, midx.data(), midx.size() * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(dt->scan_gcnt);
+    cudaFree(dt->scan_ccnt);
     cudaFree(dt->scan_gbeg);
     cudaFree(dt->scan_mcnt);
     cudaFree(dt->scan_mmask);
     cudaFree(dt->scan_midx);
     dt->scan_mcnt = nullptr;
     dt->scan_gcnt = nullptr;
+    dt->scan_ccnt = nullptr;
     dt->scan_gbeg = nullptr;
     dt->scan_mmask = nullptr;
     dt->scan_midx = nullptr;
@@ -336,6 +389,7 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
   }
   dt->scan_ngroups = ngroups;
   dt->scan_gpad = gpad;
+  dt->scan_cpad = cpad;
   dt->scan_spad = spad;
   *out = dt;
   return HP_OK;
@@ -356,6 +410,9 @@ int launch_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int
   if (rc != HP_OK) return rc;
   ScanParams p;
   p.gcnt = dt->scan_gcnt;
+  p.ccnt = dt->scan_ccnt;
+  p.nclusters = (dt->scan_ngroups + 31) / 32;
+  p.cpad = dt->scan_cpad;
   p.gbeg = dt->scan_gbeg;
   p.mcnt = dt->scan_mcnt;
   p.mmask = dt->scan_mmask;
