@@ -287,6 +287,8 @@ int hp_designability_noalloc(const int32_t* d_phen, uint64_t count, int32_t S, u
  * for p in [0, S); index S stands for the deleterious phenotype.  Robustness
  * rho_p = d_neutral[p] / (N * N_p) and phi_del = d_to_del[p] / (N * N_p).
  *   d_phen: device int32[2^N]; d_neutral, d_to_del: device uint64[S + 1].
+ * Takes stream-ordered scratch on `stream` (the error word and 16 replicas of
+ * the counters, 256 S bytes; without it the counters are updated directly).
  * Synchronises `stream` (error word: HP_EINVAL for entries outside [-1, S)). */
 int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64_t* d_neutral, uint64_t* d_to_del,
                   void* stream);
