@@ -94,6 +94,7 @@ extern "C" void hp_structs_free(hp_structs* s) {
       cudaFree(t->conf_class);
       if (t->scan_gcnt) cudaFree(t->scan_gcnt);
       if (t->scan_ccnt) cudaFree(t->scan_ccnt);
+      if (t->scan_cl1) cudaFree(t->scan_cl1);
       if (t->scan_gbeg) cudaFree(t->scan_gbeg);
       if (t->scan_mcnt) cudaFree(t->scan_mcnt);
       if (t->scan_mmask) cudaFree(t->scan_mmask);

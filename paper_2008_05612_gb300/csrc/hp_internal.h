@@ -28,7 +28,8 @@ struct DevTables {
   // per-sequence scan tables (built on first use): conformations sorted by their contact-count
   // vectors; a group is a run of equal vectors (equal A for every sequence)
   uint32_t* scan_gcnt = nullptr;   // 6 x gpad: per group the six count bit-planes, word-major
-  uint32_t* scan_ccnt = nullptr;   // 6 x cpad: per cluster of 32 groups the planes of the maxima
+  uint32_t* scan_ccnt = nullptr;   // 12 x cpad: per cluster of groups the planes of the minimum and excess
+  int32_t* scan_cl1 = nullptr;     // cpad: per cluster the largest L1 excess
   int32_t* scan_gbeg = nullptr;    // ngroups + 1: first member of each group (scan order)
   uint32_t* scan_mcnt = nullptr;   // 6 x spad: per member its count bit-planes, word-major
   uint32_t* scan_mmask = nullptr;  // NE x spad: per member its contact masks, word-major

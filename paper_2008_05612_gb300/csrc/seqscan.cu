@@ -47,11 +47,14 @@
 
 namespace {
 
-constexpr int kScanWarps = 8;  // warps (sequences in flight) per CTA
+constexpr int kScanWarps = 8;      // warps (sequences in flight) per CTA
+constexpr int kClusterGroups = 8;  // groups per cluster (four clusters per warp step)
 
 struct ScanParams {
   const uint32_t* gcnt;      // 6 x gpad count planes per group (even bits 0..2, odd bits 0..2)
-  const uint32_t* ccnt;      // 6 x cpad count planes per cluster of 32 groups (componentwise maxima)
+  const uint32_t* ccnt;      // 12 x cpad planes per cluster of kClusterGroups groups: the componentwise
+                             // minimum of its count vectors (6), the maximum excess over it (6)
+  const int32_t* cl1;        // cpad: per cluster the largest L1 excess of a member group over the minimum
   const int32_t* gbeg;       // ngroups + 1 member ranges
   const uint32_t* mcnt;      // 6 x spad count planes per member (the unpruned scan)
   const uint32_t* mmask;     // NE x spad contact masks per member
@@ -167,35 +170,38 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
     // ones are tested (the step is short and latency-bound otherwise)
     uint32_t cw[6] = {0, 0, 0, 0, 0, 0};
     int cb0 = 0, cb1 = 0;
-    auto fetch = [&](int g0, uint32_t (&c)[6], int& b0, int& b1) {
-      const int gi = g0 + lane;
-      if (gi < p.ngroups) {
+    auto fetch = [&](int gi, uint32_t (&c)[6], int& b0, int& b1) {
+      if (gi >= 0 && gi < p.ngroups) {
 #pragma unroll
         for (int k = 0; k < 6; k++) c[k] = __ldg(p.gcnt + (size_t)k * p.gpad + gi);
         b0 = __ldg(p.gbeg + gi);
         b1 = __ldg(p.gbeg + gi + 1);
       }
     };
-    // Groups come in clusters of 32 (one warp step): a cluster's componentwise-maximal count
-    // vector has A no smaller than any of its groups' (h >= 0), so when its bound falls below
-    // cut the whole cluster is skipped.  The lanes test 32 clusters at once; next_cluster walks
-    // the survivors.
+    // Groups come in clusters of kClusterGroups.  With m the componentwise minimum of a
+    // cluster's count vectors, d its largest excess over m and L its largest L1 excess, every
+    // group's A = h.m + h.(c - m) <= h.m + min(h.d, L) (h in {0,1}^N), so when the bound of that
+    // value falls below cut the whole cluster is skipped.  The lanes test 32 clusters at once;
+    // pop_cluster walks the survivors and a warp step takes four of them (lane l: cluster l / 8,
+    // group l % 8).
     int k0 = -32;
     uint32_t sv = 0;
-    auto next_cluster = [&]() -> int {
+    auto pop_cluster = [&]() -> int {
       while (sv == 0) {
         k0 += 32;
         if (k0 >= p.nclusters) return -1;
         const int ki = k0 + lane;
         bool keep = false;
         if (ki < p.nclusters) {
-          uint32_t c[6];
+          uint32_t c[12];
 #pragma unroll
-          for (int k = 0; k < 6; k++) c[k] = __ldg(p.ccnt + (size_t)k * p.cpad + ki);
-          const int A = (__popc(e & c[0]) + __popc(o & c[3])) + 2 * (__popc(e & c[1]) + __popc(o & c[4])) +
-                        4 * (__popc(e & c[2]) + __popc(o & c[5]));
+          for (int k = 0; k < 12; k++) c[k] = __ldg(p.ccnt + (size_t)k * p.cpad + ki);
+          const int Am = (__popc(e & c[0]) + __popc(o & c[3])) + 2 * (__popc(e & c[1]) + __popc(o & c[4])) +
+                         4 * (__popc(e & c[2]) + __popc(o & c[5]));
+          const int Ad = (__popc(e & c[6]) + __popc(o & c[9])) + 2 * (__popc(e & c[7]) + __popc(o & c[10])) +
+                         4 * (__popc(e & c[8]) + __popc(o & c[11]));
           n_bound++;
-          keep = upper(A, p.C) >= cut;
+          keep = upper(Am + min(Ad, __ldg(p.cl1 + ki)), p.C) >= cut;
         }
         sv = __ballot_sync(0xFFFFFFFFu, keep);
       }
@@ -203,19 +209,28 @@ __global__ void __launch_bounds__(32 * kScanWarps, 4) seq_scan_kernel(const Scan
       sv &= sv - 1;
       return cl;
     };
-    int cl = cand >= 0 ? next_cluster() : -1;
-    if (cl >= 0) fetch(cl * 32, cw, cb0, cb1);
-    while (cl >= 0) {
-      const int g0 = cl * 32;
-      cl = next_cluster();
+    // this lane's group of the next step (-1: none); false when no cluster is left
+    auto next_step = [&](int& gi) -> bool {
+      const int c0 = pop_cluster(), c1 = c0 >= 0 ? pop_cluster() : -1, c2 = c1 >= 0 ? pop_cluster() : -1,
+                c3 = c2 >= 0 ? pop_cluster() : -1;
+      const int q = lane / kClusterGroups, mine = q == 0 ? c0 : q == 1 ? c1 : q == 2 ? c2 : c3;
+      gi = mine >= 0 ? mine * kClusterGroups + lane % kClusterGroups : -1;
+      return c0 >= 0;
+    };
+    static_assert(32 / kClusterGroups == 4, "four clusters per warp step");
+    int gnext = -1;
+    bool have = cand >= 0 && next_step(gnext);
+    if (have) fetch(gnext, cw, cb0, cb1);
+    while (have) {
+      const int gi = gnext;
+      have = next_step(gnext);
       uint32_t nw[6] = {0, 0, 0, 0, 0, 0};
       int nb0 = 0, nb1 = 0;
-      if (cl >= 0) fetch(cl * 32, nw, nb0, nb1);
-      // lane l: group g0 + l, its A and bound
-      const int gi = g0 + lane;
+      if (have) fetch(gnext, nw, nb0, nb1);
+      // lane l: its group gi, A and bound
       int A = 0, n = 0;
       const int beg = cb0;
-      if (gi < p.ngroups) {
+      if (gi >= 0 && gi < p.ngroups) {
         A = (__popc(e & cw[0]) + __popc(o & cw[3])) + 2 * (__popc(e & cw[1]) + __popc(o & cw[4])) +
             4 * (__popc(e & cw[2]) + __popc(o & cw[5]));
         n_bound++;
@@ -300,7 +315,7 @@ namespace hp {
 // counts, so equal vectors form contiguous groups.  The order interleaves the
 // counts' bits (the high bit of every residue's count, then the middle bits,
 // then the low bits), so that the 32 groups of a cluster have similar counts in
-// every residue and the cluster's componentwise maximum stays tight.
+// every residue and the cluster's bound stays tight.
 int scan_tables(const hp_structs* cs, DevTables** out) {
   DevTables* dt = nullptr;
   int rc = device_tables(cs, &dt);
@@ -331,16 +346,30 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
   const int ngroups = (int)gbeg.size();
   gbeg.push_back((int32_t)order.size());
   const int gpad = (ngroups + 31) / 32 * 32, spad = (s->S_dir + 31) / 32 * 32;
-  const int nclusters = (ngroups + 31) / 32, cpad = (nclusters + 31) / 32 * 32;
-  std::vector<uint32_t> ccnt((size_t)6 * cpad, 0u);
+  const int nclusters = (ngroups + kClusterGroups - 1) / kClusterGroups, cpad = (nclusters + 31) / 32 * 32;
+  std::vector<uint32_t> ccnt((size_t)12 * cpad, 0u);
+  std::vector<int32_t> cl1(cpad, 0);
   for (int cl = 0; cl < nclusters; cl++) {
-    std::vector<uint8_t> mx(N, 0);
-    for (int gi = 32 * cl; gi < std::min(ngroups, 32 * cl + 32); gi++)
-      for (int i = 0; i < N; i++) mx[i] = std::max(mx[i], cvec[order[gbeg[gi]]][i]);
-    // even residue 2k -> bit k of the even planes, odd residue 2k + 1 -> bit k of the odd planes
+    const int g0 = kClusterGroups * cl, g1 = std::min(ngroups, g0 + kClusterGroups);
+    std::vector<uint8_t> mn(N, 255), mx(N, 0);
+    for (int gi = g0; gi < g1; gi++)
+      for (int i = 0; i < N; i++) {
+        mn[i] = std::min(mn[i], cvec[order[gbeg[gi]]][i]);
+        mx[i] = std::max(mx[i], cvec[order[gbeg[gi]]][i]);
+      }
+    for (int gi = g0; gi < g1; gi++) {
+      int l1 = 0;
+      for (int i = 0; i < N; i++) l1 += cvec[order[gbeg[gi]]][i] - mn[i];
+      cl1[cl] = std::max(cl1[cl], l1);
+    }
+    // even residue 2k -> bit k of the even planes, odd residue 2k + 1 -> bit k of the odd planes;
+    // planes 0..5 the minimum, 6..11 the largest excess
     for (int i = 0; i < N; i++)
-      for (int b = 0; b < 3; b++)
-        if ((mx[i] >> b) & 1) ccnt[(size_t)((i & 1) ? 3 + b : b) * cpad + cl] |= 1u << (i >> 1);
+      for (int b = 0; b < 3; b++) {
+        const size_t plane = (i & 1) ? 3 + b : b;
+        if ((mn[i] >> b) & 1) ccnt[plane * cpad + cl] |= 1u << (i >> 1);
+        if (((mx[i] - mn[i]) >> b) & 1) ccnt[(6 + plane) * cpad + cl] |= 1u << (i >> 1);
+      }
   }
   std::vector<uint32_t> gcnt((size_t)6 * gpad, 0u), mcnt((size_t)6 * spad, 0u), mmask((size_t)std::max(NE, 1) * spad, 0u);
   std::vector<int32_t> midx(spad, -1);
@@ -363,6 +392,8 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
   cudaError_t e = cudaMalloc(&dt->scan_gcnt, gcnt.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&dt->scan_ccnt, ccnt.size() * 4);
   if (e == cudaSuccess) e = cudaMemcpy(dt->scan_ccnt, ccnt.data(), ccnt.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&dt->scan_cl1, cl1.size() * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(dt->scan_cl1, cl1.data(), cl1.size() * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&dt->scan_gbeg, gbeg.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&dt->scan_mcnt, mcnt.size() * 4);
   if (e == cudaSuccess) e = cudaMalloc(&dt->scan_mmask, mmask.size() * 4);
@@ -375,6 +406,7 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
   if (e != cudaSuccess) {
     cudaFree(dt->scan_gcnt);
     cudaFree(dt->scan_ccnt);
+    cudaFree(dt->scan_cl1);
     cudaFree(dt->scan_gbeg);
     cudaFree(dt->scan_mcnt);
     cudaFree(dt->scan_mmask);
@@ -382,6 +414,7 @@ int scan_tables(const hp_structs* cs, DevTables** out) {
     dt->scan_mcnt = nullptr;
     dt->scan_gcnt = nullptr;
     dt->scan_ccnt = nullptr;
+    dt->scan_cl1 = nullptr;
     dt->scan_gbeg = nullptr;
     dt->scan_mmask = nullptr;
     dt->scan_midx = nullptr;
@@ -411,7 +444,8 @@ int launch_scan(const hp_structs* s, const uint64_t* d_ids, int64_t n, const int
   ScanParams p;
   p.gcnt = dt->scan_gcnt;
   p.ccnt = dt->scan_ccnt;
-  p.nclusters = (dt->scan_ngroups + 31) / 32;
+  p.cl1 = dt->scan_cl1;
+  p.nclusters = (dt->scan_ngroups + kClusterGroups - 1) / kClusterGroups;
   p.cpad = dt->scan_cpad;
   p.gbeg = dt->scan_gbeg;
   p.mcnt = dt->scan_mcnt;
