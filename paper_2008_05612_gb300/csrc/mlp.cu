@@ -565,7 +565,7 @@ struct hp_mlp {
   bf16 *dZ = nullptr, *dZT = nullptr, *dA2 = nullptr, *dA2T = nullptr, *dA1 = nullptr, *dA1T = nullptr;
   int32_t* labels = nullptr;
   unsigned* tc_err = nullptr;  // set by a tcgen05 GEMM whose bounded mbarrier wait gave up
-  // fused top-k: per row up to 16 candidates of each of up to 2 lists per 256-class tile
+  // fused top-k: per row and 256-class tile range up to 32 candidates (2 lists of up to 16)
   float* cand_v = nullptr;
   int32_t* cand_i = nullptr;
   // column-sum partials (max_batch / 32 + 1 chunks x the widest layer: 256-row chunks of the
@@ -943,7 +943,7 @@ extern "C" int hp_mlp_create(int32_t N, int32_t H1, int32_t H2, int32_t S, int32
   }
   al(&m->labels, B * 4);
   al(&m->tc_err, sizeof(unsigned));
-  const size_t ncand = (size_t)max_batch * ((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcListsPerTile * 16;
+  const size_t ncand = (size_t)max_batch * ((S + hp::kTcTileN - 1) / hp::kTcTileN) * hp::kTcTopkSlotsPerTile;
   al(&m->cand_v, ncand * 4);
   al(&m->cand_i, ncand * 4);
   al(&m->colws, (size_t)(B / 32 + 1) * std::max(m->Spad, std::max(H1, H2)) * 4);
@@ -1101,7 +1101,7 @@ extern "C" int hp_mlp_topk(hp_mlp* m, const uint64_t* d_ids, int64_t n, int32_t 
       ep.col_id = m->perm;
       if (rc == HP_OK) rc = hp::tc_gemm(m->Hb2, m->H2, m->w3p, m->H2, nb, m->S, m->H2, ep, m->tc_err, st);
       if (rc != HP_OK) return rc;
-      hp::tc_topk_merge(m->cand_v, m->cand_i, hp::tc_topk_lists(nb, m->S), nb, ep.kt, k, m->S, d_top + off * k, st);
+      hp::tc_topk_merge(m->cand_v, m->cand_i, hp::tc_topk_lists(nb, m->S, ep.kt), nb, ep.kt, k, m->S, d_top + off * k, st);
     } else {
       int rc = forward(m, ids, nb, rows, st);
       if (rc != HP_OK) return rc;

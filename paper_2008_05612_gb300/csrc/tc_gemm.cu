@@ -40,14 +40,14 @@ constexpr int SX_FLOATS = 32 * 32;  // top-k mode: one epilogue warp's staged lo
 // gradient mode: per epilogue warp two staging buffers, each a 32 x 32 bf16 block of dz
 // (row-major, 64-byte rows), the sources of the TMA stores
 constexpr int STG_BLOCK = 32 * 32 * 2, STG_WARP = 2 * STG_BLOCK;
-// Epilogue warps: in top-k mode 8, two per tensor-memory lane quarter, 128 columns each (one
-// candidate list per row and warp); otherwise 16, four per lane quarter, 64 columns each (more
-// warps hide the tensor-memory and global-memory latencies of the heavier epilogues).  Top-k and
+// Epilogue warps: 16, four per tensor-memory lane quarter, 64 columns each (more warps hide the
+// tensor-memory and global-memory latencies of the epilogues), except in top-k mode, which keeps
+// 8 (two per lane quarter, 128 columns each; each warp keeps one candidate list per row).  Top-k and
 // softmax modes also keep the warp's biases of the current tile in shared memory; a 3-stage ring
 // leaves room for the warps' shared-memory areas.
 template <int KT>
 struct Shape {
-  static constexpr int kEpiWarps = KT > 0 ? 4 * kTcListsPerTile : 16;
+  static constexpr int kEpiWarps = KT > 0 ? 4 * tc_topk_lists_per_tile(KT) : 16;
   static constexpr int kThreads = 64 + 32 * kEpiWarps;
   static constexpr int kColsPerWarp = TN / (kEpiWarps / 4);
   static constexpr int kStages = 3;
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
         const int row = rbase + lane;
         if (ok && row < p.M) {
           // list l = 2 r + h of this row
-          const size_t off = ((size_t)(w.r * kTcListsPerTile + h) * p.M + row) * KT;
+          const size_t off = ((size_t)(w.r * tc_topk_lists_per_tile(KT) + h) * p.M + row) * KT;
 #pragma unroll
           for (int j = 0; j < KT; j += 4) {
             *reinterpret_cast<float4*>(ep.cand_v + off + j) = make_float4(bv[j], bv[j + 1], bv[j + 2], bv[j + 3]);
@@ -874,14 +874,17 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mdz
 
 }  // namespace
 
-int tc_stats_lists(int M, int N) { return tc_topk_lists(M, N) / kTcListsPerTile * kTcStatsListsPerTile; }
-
-int tc_topk_lists(int M, int N) {
-  // as many column ranges as make the units a multiple of the SM count (balanced waves), times
-  // the two column slices of each tile (one list per epilogue warp)
+// column ranges of the top-k and statistics modes: as many as make the units a multiple of the
+// SM count (balanced waves)
+int tc_ranges(int M, int N) {
   const int mt = (M + TM - 1) / TM, nt = (N + TN - 1) / TN, g = sm_count();
-  return std::max(1, std::min(nt, g / std::gcd(mt, g))) * kTcListsPerTile;
+  return std::max(1, std::min(nt, g / std::gcd(mt, g)));
 }
+
+int tc_stats_lists(int M, int N) { return tc_ranges(M, N) * kTcStatsListsPerTile; }
+
+int tc_topk_lists(int M, int N, int kt) { return tc_ranges(M, N) * tc_topk_lists_per_tile(kt); }
+
 
 int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const TcEpilogue& ep, unsigned* err,
             cudaStream_t st) {
@@ -910,7 +913,7 @@ int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
     return fail(HP_EINVAL, "tc_gemm: split-K needs store mode with an fp32 output only and at most one slice per K chunk");
   Params p{M, N, K, (M + TM - 1) / TM, (N + TN - 1) / TN, 0, 0, ep.ksplit, 0, ep.a_mn ? 1 : 0, ep.b_mn ? 1 : 0, ep, err,
            (uint32_t)std::min<long long>(wait_limit(SPIN_LIMIT), 0xFFFFFFFFll)};
-  p.nr = (ep.kt > 0 || ep.kt == -1) ? tc_topk_lists(M, N) / kTcListsPerTile : p.nt;
+  p.nr = (ep.kt > 0 || ep.kt == -1) ? tc_ranges(M, N) : p.nt;
   p.nfast = ep.kt == 0 && M > N;
   p.units = p.mt * p.nr * p.ksplit;
   switch (ep.kt) {

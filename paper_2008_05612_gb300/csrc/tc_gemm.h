@@ -14,8 +14,11 @@
 namespace hp {
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
-constexpr int kTcListsPerTile = 2;       // top-k mode: candidate lists per row and 256-column tile range
 constexpr int kTcStatsListsPerTile = 4;  // row-statistics mode: lists per row and tile range
+constexpr int kTcTopkSlotsPerTile = 32;  // top-k mode: candidate slots per row and tile range (lists x kt)
+// top-k mode: candidate lists per row and 256-column tile range, one per epilogue warp of a
+// tensor-memory lane quarter (two; four, with 16 epilogue warps, measured 4 % slower for k = 4)
+__host__ __device__ constexpr int tc_topk_lists_per_tile(int) { return 2; }
 
 struct TcEpilogue {
   bool a_mn = false, b_mn = false;  // operand layouts (see above)
@@ -26,7 +29,8 @@ struct TcEpilogue {
   __nv_bfloat16* Cb = nullptr;  // bf16 output [M x ldcb] or null
   int ldcb = 0;
   // top-k mode (kt in {4, 8, 16}, outputs ignored): the columns are split into
-  // L = tc_topk_lists(M, N) disjoint sets (unions of 128-column slices of the 256-column tiles);
+  // L = tc_topk_lists(M, N, kt) disjoint sets (unions of 128-column slices of the 256-column
+  // tiles);
   // per row r and set l, the kt largest values with their column indices, sorted (value
   // descending, index ascending), go to cand_v / cand_i [(l * M + r) * kt + j]; missing entries
   // are (-inf, INT32_MAX)
@@ -80,8 +84,9 @@ struct TcEpilogue {
 int tc_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K, const TcEpilogue& ep,
             unsigned* err, cudaStream_t st);
 
-// Number of candidate lists per row that top-k mode writes (at most 2 ceil(N / 256)).
-int tc_topk_lists(int M, int N);
+// Number of candidate lists per row that top-k mode writes (at most
+// tc_topk_lists_per_tile(kt) ceil(N / 256)).
+int tc_topk_lists(int M, int N, int kt);
 
 // Number of statistics lists per row that row-statistics mode writes (at most 4 ceil(N / 256)).
 int tc_stats_lists(int M, int N);
