@@ -307,13 +307,28 @@ __global__ void cc_init(const int32_t* __restrict__ phen, unsigned long long tot
 }
 
 // Root of x: parents always have smaller ids, so the walk terminates.
-__device__ __forceinline__ int32_t cc_find(const int32_t* label, int32_t x) {
+__device__ __forceinline__ int32_t cc_root(const int32_t* label, int32_t x) {
   int32_t par = __ldcg(label + x);
   while (par != x) {
     x = par;
     par = __ldcg(label + x);
   }
   return x;
+}
+
+// The same with path halving, while components are being joined: each visited id is pointed at
+// its grandparent (an ancestor with a smaller id, so concurrent finds and hooks stay correct;
+// hooks only change roots, which are never rewritten).  Not for the final compression, where a
+// late halving write could replace an id's final root by a non-root ancestor.
+__device__ __forceinline__ int32_t cc_find(int32_t* label, int32_t x) {
+  for (;;) {
+    const int32_t q = __ldcg(label + x);
+    if (q == x) return x;
+    const int32_t g = __ldcg(label + q);
+    if (g == q) return q;
+    __stcg(label + x, g);
+    x = g;
+  }
 }
 
 // Lock-free union of the components of a and b: hook the larger root under the smaller one with
@@ -361,7 +376,7 @@ __global__ void cc_finish(const int32_t* __restrict__ phen, unsigned long long t
   for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
     const int32_t l = label[g];
     if (l < 0) continue;
-    const int32_t r = cc_find(label, (int32_t)g);
+    const int32_t r = cc_root(label, (int32_t)g);
     label[g] = r;
     if (r == (int32_t)g) atomicAdd(&ncomp[phen[g]], 1ull);
   }
@@ -451,15 +466,11 @@ extern "C" int hp_robustness(const int32_t* d_phen, int32_t N, int32_t S, uint64
 
 namespace hp {
 
-cudaError_t launch_robustness(const int32_t* d_phen, int N, int S, unsigned long long* neutral,
-                              unsigned long long* to_del, unsigned long long* negcount, unsigned* err, cudaStream_t st) {
+// The passes over the flips of an N-bit map: bits [0, k) first, then the high bits [k, N) in
+// near-equal groups of at most kRobMaxPassBits, each with the kRobTileBits - h lowest bits
+// contiguous (k = min(N, kRobTileBits)).
+std::vector<RobPass> flip_passes(int N) {
   const int k = std::min((int)N, kRobTileBits);
-  const unsigned long long blocks = 1ull << (N - k);
-  const size_t smem = 2 * (sizeof(int32_t) << kRobTileBits) + (sizeof(uint16_t) << kRobTileBits);
-  cudaError_t e = cudaFuncSetAttribute(robustness_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  // the passes: bits [0, k) first, then the high bits [k, N) in near-equal groups of at most
-  // kRobMaxPassBits, each with the kRobTileBits - h lowest bits contiguous
   std::vector<RobPass> plan;
   {
     RobPass p{};
@@ -481,6 +492,17 @@ cudaError_t launch_robustness(const int32_t* d_phen, int N, int S, unsigned long
     lo += p.h;
     plan.push_back(p);
   }
+  return plan;
+}
+
+cudaError_t launch_robustness(const int32_t* d_phen, int N, int S, unsigned long long* neutral,
+                              unsigned long long* to_del, unsigned long long* negcount, unsigned* err, cudaStream_t st) {
+  const int k = std::min((int)N, kRobTileBits);
+  const unsigned long long blocks = 1ull << (N - k);
+  const size_t smem = 2 * (sizeof(int32_t) << kRobTileBits) + (sizeof(uint16_t) << kRobTileBits);
+  cudaError_t e = cudaFuncSetAttribute(robustness_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const std::vector<RobPass> plan = flip_passes(N);
   // a few CTAs per SM walking the blocks (shared memory: two blocks each), counting into
   // replicated counters (stream-ordered scratch; without it, straight into neutral / to_del)
   const unsigned grid = (unsigned)std::min<unsigned long long>(blocks, (unsigned long long)sm_count() * 2);
