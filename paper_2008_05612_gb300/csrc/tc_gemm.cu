@@ -233,6 +233,85 @@ __device__ __forceinline__ uint32_t stg_off(int r, int b) {
   return (uint32_t)(r * 64 + ((((b >> 4) ^ (r >> 1)) & 3) << 4) + (b & 15));
 }
 
+// Top-k chunk (one row per lane, 32 columns): the logits acc + bias enter the row's running list
+// (bv, bi: value descending, index ascending) if they reach its last entry; the first full chunk
+// seeds the threshold with the smallest of KT group maxima.  Warp-collective.
+template <int KT>
+__device__ __forceinline__ void topk_chunk(uint32_t (&v)[32], const float* bias, int cmax, int colbase,
+                                           const int32_t* col_id, float (&bv)[KT], int (&bi)[KT], bool& seeded,
+                                           float* area, int lane) {
+  // 1. bias-added logits of the chunk (cmax of its columns are valid)
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    const float4 b4 = *reinterpret_cast<const float4*>(bias + j);
+    v[j] = __float_as_uint(__uint_as_float(v[j]) + b4.x);
+    v[j + 1] = __float_as_uint(__uint_as_float(v[j + 1]) + b4.y);
+    v[j + 2] = __float_as_uint(__uint_as_float(v[j + 2]) + b4.z);
+    v[j + 3] = __float_as_uint(__uint_as_float(v[j + 3]) + b4.w);
+  }
+  // 2. the columns that can enter: at least the list's current last (equal values are
+  //    settled on their ids below) or, for the list's first full chunk, at least the
+  //    smallest of KT group maxima (KT columns reach it, so nothing below it is among
+  //    the KT best)
+  float thr = nextafterf(bv[KT - 1], -INFINITY);  // x > thr  <=>  x >= last
+  if (!seeded && cmax == 32) {
+    constexpr int G = 32 / KT;
+    float t0 = INFINITY;
+#pragma unroll
+    for (int g = 0; g < KT; g++) {
+      float mg = __uint_as_float(v[g * G]);
+#pragma unroll
+      for (int e = 1; e < G; e++) mg = fmaxf(mg, __uint_as_float(v[g * G + e]));
+      t0 = fminf(t0, mg);
+    }
+    thr = nextafterf(t0, -INFINITY);  // x > thr  <=>  x >= t0
+    seeded = true;
+  }
+  uint32_t part[8];
+#pragma unroll
+  for (int g = 0; g < 8; g++) {
+    uint32_t m4 = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const float x = __uint_as_float(v[4 * g + e]);
+      m4 |= (uint32_t)(x > thr) << e;
+    }
+    part[g] = m4 << (4 * g);
+  }
+  uint32_t mask = ((part[0] | part[1]) | (part[2] | part[3])) | ((part[4] | part[5]) | (part[6] | part[7]));
+  if (cmax < 32) mask &= (1u << cmax) - 1u;
+  if (__any_sync(0xFFFFFFFFu, mask != 0)) {
+    // 3. stage the row (16-byte groups XOR-swizzled by lane: conflict-free), then
+    //    insert each lane's candidates in column order, one per lane per round
+#pragma unroll
+    for (int g = 0; g < 8; g++)
+      *reinterpret_cast<uint4*>(area + lane * 32 + ((g ^ (lane & 7)) << 2)) =
+          make_uint4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+    __syncwarp();
+    while (__any_sync(0xFFFFFFFFu, mask != 0)) {
+      if (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        float cv = area[lane * 32 + (((j >> 2) ^ (lane & 7)) << 2) + (j & 3)];
+        int ci = col_id ? __ldg(col_id + colbase + j) : colbase + j;
+        if (cv > bv[KT - 1] || (cv == bv[KT - 1] && ci < bi[KT - 1])) {
+#pragma unroll
+          for (int e = 0; e < KT; e++) {
+            const bool take = cv > bv[e] || (cv == bv[e] && ci < bi[e]);
+            const float tv = bv[e];
+            const int ti = bi[e];
+            bv[e] = take ? cv : bv[e];
+            bi[e] = take ? ci : bi[e];
+            cv = take ? tv : cv;
+            ci = take ? ti : ci;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // TMA store of a 32 x 32 bf16 box from shared memory at tensor coordinates (x, y); the part of
 // the box outside the tensor is not written
 __device__ __forceinline__ void tma_store(const CUtensorMap* map, uint32_t src, int x, int y) {
@@ -541,6 +620,27 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
               staged++;
             }
           }
+        } else if constexpr (KT > 0) {
+          // ---- top-k: chunks alternate between two register sets, the next one's tensor-memory
+          // load in flight while the current one is filtered
+          const uint32_t tbase = tmem + a * TN + ((uint32_t)(q * 32) << 16) + (uint32_t)cbeg;
+          const int nch = min(CW / 32, (p.N - n0 - cbeg + 31) / 32);
+          uint32_t va[32], vb[32];
+          __syncwarp();
+          if (nch > 0) tmem_ld32(tbase, va);
+#pragma unroll 1
+          for (int i = 0; i < nch; i += 2) {
+            if (i + 1 < nch) tmem_ld32_issue(tbase + 32 * (i + 1), vb);
+            topk_chunk<KT>(va, bsm + 32 * i, min(32, p.N - (n0 + cbeg + 32 * i)), n0 + cbeg + 32 * i, ep.col_id, bv, bi,
+                           seeded, area, lane);
+            if (i + 1 < nch) {
+              tmem_wait(vb);
+              if (i + 2 < nch) tmem_ld32_issue(tbase + 32 * (i + 2), va);
+              topk_chunk<KT>(vb, bsm + 32 * (i + 1), min(32, p.N - (n0 + cbeg + 32 * (i + 1))), n0 + cbeg + 32 * (i + 1),
+                             ep.col_id, bv, bi, seeded, area, lane);
+              if (i + 2 < nch) tmem_wait(va);
+            }
+          }
         } else {
 #pragma unroll 1
           for (int c0 = cbeg; c0 < cend && n0 + c0 < p.N; c0 += 32) {
@@ -603,78 +703,6 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
                 }
               }
               __syncwarp();
-            } else {
-              // 1. bias-added logits of the chunk
-              const int cmax = min(32, p.N - (n0 + c0));
-#pragma unroll
-              for (int j = 0; j < 32; j += 4) {
-                const float4 b4 = *reinterpret_cast<const float4*>(bsm + (c0 - cbeg) + j);
-                v[j] = __float_as_uint(__uint_as_float(v[j]) + b4.x);
-                v[j + 1] = __float_as_uint(__uint_as_float(v[j + 1]) + b4.y);
-                v[j + 2] = __float_as_uint(__uint_as_float(v[j + 2]) + b4.z);
-                v[j + 3] = __float_as_uint(__uint_as_float(v[j + 3]) + b4.w);
-              }
-              // 2. the columns that can enter: at least the list's current last (equal values are
-              //    settled on their ids below) or, for the list's first full chunk, at least the
-              //    smallest of KT group maxima (KT columns reach it, so nothing below it is among
-              //    the KT best)
-              float thr = nextafterf(bv[KT - 1], -INFINITY);  // x > thr  <=>  x >= last
-              if (!seeded && cmax == 32) {
-                constexpr int G = 32 / KT;
-                float t0 = INFINITY;
-#pragma unroll
-                for (int g = 0; g < KT; g++) {
-                  float mg = __uint_as_float(v[g * G]);
-#pragma unroll
-                  for (int e = 1; e < G; e++) mg = fmaxf(mg, __uint_as_float(v[g * G + e]));
-                  t0 = fminf(t0, mg);
-                }
-                thr = nextafterf(t0, -INFINITY);  // x > thr  <=>  x >= t0
-                seeded = true;
-              }
-              uint32_t part[8];
-#pragma unroll
-              for (int g = 0; g < 8; g++) {
-                uint32_t m4 = 0;
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                  const float x = __uint_as_float(v[4 * g + e]);
-                  m4 |= (uint32_t)(x > thr) << e;
-                }
-                part[g] = m4 << (4 * g);
-              }
-              uint32_t mask = ((part[0] | part[1]) | (part[2] | part[3])) | ((part[4] | part[5]) | (part[6] | part[7]));
-              if (cmax < 32) mask &= (1u << cmax) - 1u;
-              if (__any_sync(0xFFFFFFFFu, mask != 0)) {
-                // 3. stage the row (16-byte groups XOR-swizzled by lane: conflict-free), then
-                //    insert each lane's candidates in column order, one per lane per round
-#pragma unroll
-                for (int g = 0; g < 8; g++)
-                  *reinterpret_cast<uint4*>(area + lane * 32 + ((g ^ (lane & 7)) << 2)) =
-                      make_uint4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
-                __syncwarp();
-                while (__any_sync(0xFFFFFFFFu, mask != 0)) {
-                  if (mask) {
-                    const int j = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    float cv = area[lane * 32 + (((j >> 2) ^ (lane & 7)) << 2) + (j & 3)];
-                    int ci = ep.col_id ? __ldg(ep.col_id + n0 + c0 + j) : n0 + c0 + j;
-                    if (cv > bv[KT - 1] || (cv == bv[KT - 1] && ci < bi[KT - 1])) {
-#pragma unroll
-                      for (int e = 0; e < KT; e++) {
-                        const bool take = cv > bv[e] || (cv == bv[e] && ci < bi[e]);
-                        const float tv = bv[e];
-                        const int ti = bi[e];
-                        bv[e] = take ? cv : bv[e];
-                        bi[e] = take ? ci : bi[e];
-                        cv = take ? tv : cv;
-                        ci = take ? ti : ci;
-                      }
-                    }
-                  }
-                }
-                __syncwarp();
-              }
             }
           }
         }
