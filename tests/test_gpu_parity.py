@@ -227,8 +227,11 @@ def test_neighbourhood_rows_match_oracle(hp, obox, dims):
                                       oracle.neighbourhood(want, s.N, s.S, q))
 
 
-@pytest.mark.parametrize("N,S,seed", [(12, 5, 1), (20, 300, 2), (24, 51704, 3)])
+@pytest.mark.parametrize("N,S,seed", [(1, 2, 8), (3, 3, 9), (12, 5, 1), (17, 40, 5), (20, 300, 2), (21, 1000, 4),
+                                     (24, 51704, 3)])
 def test_reductions_on_synthetic_maps(hp, N, S, seed):
+    """Maps below one 2^13-id block (N = 1, 3), one block, and one or two later flip passes of 4 to 8
+    high bits (N = 17: one pass of 4; 21: one of 8, the shortest contiguous runs; 24: two)."""
     m = synthetic_map(N, S, seed)
     phen = torch.from_numpy(m).cuda()
     np.testing.assert_array_equal(hp.designability(phen, S).cpu().numpy().astype(np.uint64), oracle.designability(m, S))
