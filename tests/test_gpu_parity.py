@@ -277,3 +277,21 @@ def test_small_role_shapes_equal_the_14_role_shape(hp, obox, dims, begin, bits):
     off = inputs.sample_ids(bits, 300, seed=bits + 17)
     np.testing.assert_array_equal(auto.cpu().numpy()[off.astype(np.int64)],
                                   obox(dims).phenotypes(off + np.uint64(begin)))
+
+
+def test_reductions_of_a_map_not_16_byte_aligned(hp):
+    """The robustness passes copy blocks with 16-byte asynchronous copies only from a 16-byte aligned
+    map; a map at a 4-byte offset takes the word-by-word path and gives the same counts."""
+    N, S = 20, 300
+    m = synthetic_map(N, S, 11)
+    phen = torch.from_numpy(m).cuda()
+    big = torch.empty(m.size + 1, dtype=torch.int32, device="cuda")
+    big[1:] = phen
+    shifted = big[1:]
+    assert shifted.data_ptr() % 16 != 0
+    gn, gd = hp.robustness(phen, N, S)
+    sn, sd = hp.robustness(shifted, N, S)
+    assert torch.equal(gn, sn) and torch.equal(gd, sd)
+    on, od = oracle.robustness(m, N, S)
+    np.testing.assert_array_equal(sn.cpu().numpy().astype(np.uint64), on)
+    np.testing.assert_array_equal(sd.cpu().numpy().astype(np.uint64), od)
