@@ -786,13 +786,15 @@ int backward_tc(hp_mlp* m, int rows, cudaStream_t st, const AdamStep* adam) {
   colsum(m->dA2, H2, rows, H2, m->g[3], m->colws, st);
   if (rc == HP_OK) rc = weight_grad(m, m->dA2, H2, m->Hb1, H1, H2, H1, rows, m->g[2], st);
   {
+    // dA1 = (dA2 W2) * (H1 > 0), the ReLU's backward step in the GEMM's epilogue
     hp::TcEpilogue ep;
     ep.b_mn = true;
-    ep.Cf = m->dHf;
-    ep.ldcf = H1;
+    ep.Cb = m->dA1;
+    ep.ldcb = H1;
+    ep.relu_mask = m->Hb1;
+    ep.ldmask = H1;
     if (rc == HP_OK) rc = hp::tc_gemm(m->dA2, H2, m->w2b, H1, rows, H1, H2, ep, m->tc_err, st);
   }
-  relu_backward<<<grid_for((size_t)rows * H1), 256, 0, st>>>(m->dHf, m->Hb1, m->dA1, (size_t)rows * H1);
   // layer 1
   colsum(m->dA1, H1, rows, H1, m->g[1], m->colws, st);
   if (rc == HP_OK) rc = weight_grad(m, m->dA1, H1, m->X, Kin, H1, Kin, rows, m->g[0], st);

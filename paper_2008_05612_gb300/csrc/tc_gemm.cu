@@ -698,6 +698,7 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
                   const size_t row = (size_t)(rbase + r);
                   float x = area[r * 33 + lane] + bl;
                   if (ep.relu) x = fmaxf(x, 0.f);
+                  if (ep.relu_mask && !(__bfloat162float(ep.relu_mask[row * ep.ldmask + cl]) > 0.f)) x = 0.f;
                   if (ep.Cf) ep.Cf[(size_t)w.ks * ep.split_stride + row * ep.ldcf + cl] = x;
                   if (ep.Cb) ep.Cb[row * ep.ldcb + cl] = __float2bfloat16(x);
                 }
@@ -812,9 +813,9 @@ __global__ void softmax_finish_kernel(const float* __restrict__ stats, int lists
                                       const float* __restrict__ zlab, float* __restrict__ row_m, float* __restrict__ row_inv,
                                       float* __restrict__ loss) {
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (r >= rows) return;
+  const bool row_ok = r < rows;  // whole warps past the last row still meet the block barrier below
   float m = -INFINITY, s = 0.f;
-  for (int l = lane; l < lists; l += 32) {
+  for (int l = lane; row_ok && l < lists; l += 32) {
     const float2 q = *reinterpret_cast<const float2*>(stats + 2 * ((size_t)l * rows + r));
     if (q.x == -INFINITY) continue;
     const float nm = fmaxf(m, q.x);
@@ -828,10 +829,19 @@ __global__ void softmax_finish_kernel(const float* __restrict__ stats, int lists
     if (nm != -INFINITY) s = (m == -INFINITY ? 0.f : s * __expf(m - nm)) + (om == -INFINITY ? 0.f : os * __expf(om - nm));
     m = nm;
   }
-  if (lane == 0) {
+  if (lane == 0 && row_ok) {
     row_m[r] = m;
     row_inv[r] = 1.f / s;
-    if (labels && labels[r] >= 0) atomicAdd(loss, logf(s) + m - zlab[r]);
+  }
+  // the rows' cross-entropies: summed over the block's rows, one atomic add per block (a single
+  // address takes every add)
+  __shared__ float part[32];
+  if (lane == 0) part[threadIdx.x >> 5] = (row_ok && labels && labels[r] >= 0) ? logf(s) + m - zlab[r] : 0.f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+    if (labels && t != 0.f) atomicAdd(loss, t);
   }
 }
 
@@ -927,6 +937,8 @@ int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
                       reinterpret_cast<uintptr_t>(ep.dz) % 16))
     return fail(HP_EINVAL, "tc_gemm: gradient mode needs row statistics, labels and dz (strides a multiple of 8, 16-byte aligned)");
   if (ep.kt < -2) return fail(HP_EINVAL, "tc_gemm: unknown epilogue mode");
+  if (ep.relu_mask && (ep.kt || ep.adam_w || ep.ksplit != 1 || ep.ldmask < N))
+    return fail(HP_EINVAL, "tc_gemm: the ReLU-mask epilogue takes a plain store-mode GEMM");
   if (ep.adam_w && (ep.kt || ep.Cf || ep.bias || ep.relu || ep.ksplit != 1 || !ep.adam_m || !ep.adam_v || ep.ldcf < N ||
                     (ep.wt && ep.ldwt < M)))
     return fail(HP_EINVAL, "tc_gemm: the Adam epilogue takes a plain store-mode GEMM and its moment buffers");

@@ -61,6 +61,10 @@ struct TcEpilogue {
   __nv_bfloat16* dz = nullptr;
   int ldz = 0;
   float* colpart = nullptr;
+  // store mode: if set, an element whose activation relu_mask[r * ldmask + c] (bf16) is not
+  // positive is stored as 0 (the backward step of a ReLU layer)
+  const __nv_bfloat16* relu_mask = nullptr;
+  int ldmask = 0;
   // store mode with an Adam step in place of the fp32 store (no bias, ReLU or split-K): the tile
   // is the gradient g of the fp32 weights adam_w [M x ldcf] with moments adam_m, adam_v (same
   // layout); per element m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
