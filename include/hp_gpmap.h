@@ -227,8 +227,13 @@ void hp_mlp_free(hp_mlp* m);
 int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t* d_labels, int32_t n, float* const* h_grads,
                      float* h_loss, void* stream);
 
-/* One Adam step on n (<= max_batch) ids / labels with learning rate lr; the
- * mean loss before the step goes to *h_loss if non-NULL (synchronises). */
+/* One Adam step (Kingma & Ba; b1 0.9, b2 0.999, eps 1e-8, bias-corrected) on
+ * n (<= max_batch) ids / labels with learning rate lr; the mean loss before
+ * the step goes to *h_loss if non-NULL (synchronises).  The step is the one
+ * hp_mlp_gradients' gradients give (the output layer's update is applied
+ * inside the GEMM that forms its gradient).  The next hp_mlp_topk refreshes
+ * the output layer's class-scattered copy first, on its own stream: order a
+ * train step and a top-k on different streams yourself. */
 int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t* d_labels, int32_t n, float lr, float* h_loss,
                       void* stream);
 
