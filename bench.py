@@ -684,6 +684,7 @@ def main():
     # step computes (two sets of buffers); the timed region ends when the last copy has landed
     copy_stream = torch.cuda.Stream()
     d_phen = [phen, torch.empty(nseq, dtype=torch.int32, device="cuda")]
+    d_label = [torch.empty(nseq, dtype=torch.int32, device="cuda") for _ in range(2)]
     h_phen = [torch.empty(nseq, dtype=torch.int32, pin_memory=True) for _ in range(2)]
     h_label = [torch.empty(nseq, dtype=torch.int32, pin_memory=True) for _ in range(2)]
     h_small = [[torch.empty(S + 1, dtype=torch.int64, pin_memory=True) for _ in range(3)] +
@@ -703,7 +704,7 @@ def main():
         hp.phenotype_map(s, 0, nseq, out=d_phen[b])
         hist_d = hp.designability(d_phen[b], S)
         neutral, to_del = hp.robustness(d_phen[b], N, S)
-        label, ncomp = hp.neutral_components(d_phen[b], N, S)
+        label, ncomp = hp.neutral_components(d_phen[b], N, S, out_label=d_label[b])
         ready = torch.cuda.Event()
         ready.record(stream)
         copy_stream.wait_event(ready)

@@ -504,13 +504,19 @@ def _cuda_ready():
         return False
 
 
-def neutral_components(phen, N: int, S: int, stream=None):
-    """(label[2^N], ncomp[S]) of the neutral networks (hp_neutral_components)."""
+def neutral_components(phen, N: int, S: int, stream=None, out_label=None):
+    """(label[2^N], ncomp[S]) of the neutral networks (hp_neutral_components); the labels go to
+    out_label (int32[2^N] on the map's device) when it is given."""
     import torch
 
     if phen.numel() != (1 << N):
         raise ValueError("components need the full map of 2^N sequences")
-    label = torch.empty(1 << N, dtype=torch.int32, device=phen.device)
+    if out_label is not None:
+        if out_label.dtype != torch.int32 or out_label.numel() != (1 << N) or out_label.device != phen.device:
+            raise HPError(HP_EINVAL, "neutral_components: out_label must be int32[2^N] on the map's device")
+        label = out_label
+    else:
+        label = torch.empty(1 << N, dtype=torch.int32, device=phen.device)
     ncomp = torch.empty(S, dtype=torch.int64, device=phen.device)
     _check(lib().hp_neutral_components(_dptr(phen, torch.int32, "phen"), N, S, _dptr(label, torch.int32, "label"),
                                        _dptr(ncomp, torch.int64, "ncomp"), _stream_ptr(stream)))

@@ -295,3 +295,16 @@ def test_reductions_of_a_map_not_16_byte_aligned(hp):
     on, od = oracle.robustness(m, N, S)
     np.testing.assert_array_equal(sn.cpu().numpy().astype(np.uint64), on)
     np.testing.assert_array_equal(sd.cpu().numpy().astype(np.uint64), od)
+
+
+def test_component_labels_into_a_given_buffer(hp):
+    N, S = 12, 5
+    m = synthetic_map(N, S, 13)
+    phen = torch.from_numpy(m).cuda()
+    label, ncomp = hp.neutral_components(phen, N, S)
+    buf = torch.full((1 << N,), 7, dtype=torch.int32, device="cuda")
+    l2, c2 = hp.neutral_components(phen, N, S, out_label=buf)
+    assert l2.data_ptr() == buf.data_ptr()
+    assert torch.equal(l2, label) and torch.equal(c2, ncomp)
+    with pytest.raises(hp.HPError):
+        hp.neutral_components(phen, N, S, out_label=buf[:-1])
