@@ -49,7 +49,18 @@ __global__ void __launch_bounds__(kHistThreads) hist_partial(const int32_t* __re
   if (vec4) {
     const int4* v = reinterpret_cast<const int4*>(phen);
     const unsigned long long nv = count / 4;
-    for (unsigned long long k = t0; k < nv; k += stride) {
+    // four 16-byte loads of a thread in flight together, then their ids binned
+    unsigned long long k = t0;
+    for (; k + 3 * stride < nv; k += 4 * stride) {
+      int4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) q[u] = __ldcs(v + k + u * stride);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        take(q[u].x); take(q[u].y); take(q[u].z); take(q[u].w);
+      }
+    }
+    for (; k < nv; k += stride) {
       const int4 q = __ldcs(v + k);
       take(q.x); take(q.y); take(q.z); take(q.w);
     }
