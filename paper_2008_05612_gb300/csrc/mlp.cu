@@ -287,10 +287,13 @@ __global__ void cast_bf16(const float* __restrict__ in, bf16* __restrict__ out, 
     out[i] = __float2bfloat16(in[i]);
 }
 
-// X[b, i] = bit i of ids[b] (1 = H) for i < N, 0 for i in [N, Kin) and for rows b >= n
-__global__ void encode_bits(const unsigned long long* __restrict__ ids, int n, int rows, int N, int Kin, bf16* __restrict__ X) {
+// X[b, i] = bit i of ids[b] (1 = H) for i < N, 0 for i in [N, Kin) and for rows b >= n; with
+// lab_out set, also lab_out[b] = lab_in[b] for b < n and -1 for the padding rows
+__global__ void encode_bits(const unsigned long long* __restrict__ ids, int n, int rows, int N, int Kin, bf16* __restrict__ X,
+                            const int32_t* __restrict__ lab_in, int32_t* __restrict__ lab_out) {
   const int b = blockIdx.x * blockDim.y + threadIdx.y;
   if (b >= rows) return;
+  if (lab_out && threadIdx.x == 0) lab_out[b] = b < n ? lab_in[b] : -1;
   const unsigned long long g = b < n ? ids[b] : 0ull;
   for (int i = threadIdx.x; i < Kin; i += blockDim.x)
     X[(size_t)b * Kin + i] = __float2bfloat16((b < n && i < N && ((g >> i) & 1ull)) ? 1.f : 0.f);
@@ -413,22 +416,42 @@ __global__ void colsum_final(const float* __restrict__ part, int chunks, int col
   }
 }
 
-// out = the sum of the split-K partial products (fp32)
+// out = the sum of the split-K partial products (fp32), slices added in order; four elements per
+// thread and step (n and stride multiples of 4, 16-byte aligned buffers)
 __global__ void splitk_sum(const float* __restrict__ part, int splits, size_t stride, float* __restrict__ out, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    float v = 0.f;
-    for (int k = 0; k < splits; k++) v += part[k * stride + i];
-    out[i] = v;
+  for (size_t i = 4 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x); i < n; i += 4 * (size_t)gridDim.x * blockDim.x) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(part + i));
+    for (int k = 1; k < splits; k++) {
+      const float4 t = __ldcs(reinterpret_cast<const float4*>(part + k * stride + i));
+      v.x += t.x;
+      v.y += t.y;
+      v.z += t.z;
+      v.w += t.w;
+    }
+    *reinterpret_cast<float4*>(out + i) = v;
   }
 }
 
-// dA = (sum of the split-K partial products) * (H > 0), bf16 out
+// dA = (sum of the split-K partial products) * (H > 0), bf16 out; four elements per thread and
+// step as above
 __global__ void splitk_relu_backward(const float* __restrict__ part, int splits, size_t stride, const bf16* __restrict__ H,
                                      bf16* __restrict__ dA, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    float v = 0.f;
-    for (int k = 0; k < splits; k++) v += part[k * stride + i];
-    dA[i] = __float2bfloat16(__bfloat162float(H[i]) > 0.f ? v : 0.f);
+  for (size_t i = 4 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x); i < n; i += 4 * (size_t)gridDim.x * blockDim.x) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(part + i));
+    for (int k = 1; k < splits; k++) {
+      const float4 t = __ldcs(reinterpret_cast<const float4*>(part + k * stride + i));
+      v.x += t.x;
+      v.y += t.y;
+      v.z += t.z;
+      v.w += t.w;
+    }
+    const uint2 h = *reinterpret_cast<const uint2*>(H + i);
+    const float hx = __uint_as_float(h.x << 16), hy = __uint_as_float(h.x & 0xFFFF0000u);
+    const float hz = __uint_as_float(h.y << 16), hw = __uint_as_float(h.y & 0xFFFF0000u);
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(hx > 0.f ? v.x : 0.f, hy > 0.f ? v.y : 0.f);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn(hz > 0.f ? v.z : 0.f, hw > 0.f ? v.w : 0.f);
+    *reinterpret_cast<uint2*>(dA + i) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
   }
 }
 
@@ -450,17 +473,33 @@ __global__ void relu_backward(const float* __restrict__ dH, const bf16* __restri
     dA[i] = __float2bfloat16(__bfloat162float(H[i]) > 0.f ? dH[i] : 0.f);
 }
 
-__global__ void adam_update(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                            bf16* __restrict__ wb, size_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+// The parameter tensors one Adam launch updates: tensor t holds the elements [end[t-1], end[t])
+// of one flat index space (end[-1] = 0)
+struct AdamSet {
+  float* w[6];
+  const float* g[6];
+  float* m[6];
+  float* v[6];
+  bf16* wb[6];  // bf16 copy of w, or null
+  size_t end[6];
+  int count;
+};
+
+__global__ void adam_update(AdamSet s, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const size_t n = s.end[s.count - 1];
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    int t = 0;
+    while (k >= s.end[t]) t++;
+    const size_t i = k - (t ? s.end[t - 1] : 0);
+    float *w = s.w[t], *m = s.m[t], *v = s.v[t];
+    const float gi = s.g[t][i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
     const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
     w[i] = wi;
-    if (wb) wb[i] = __float2bfloat16(wi);
+    if (s.wb[t]) s.wb[t][i] = __float2bfloat16(wi);
   }
 }
 
@@ -676,7 +715,7 @@ int weight_grad(hp_mlp* m, const bf16* dA, int lda, const bf16* H, int ldb, int 
   ep.ksplit = ks;
   ep.split_stride = (size_t)M * N;
   const int rc = hp::tc_gemm(dA, lda, H, ldb, M, N, K, ep, m->tc_err, st);
-  if (rc == HP_OK) splitk_sum<<<grid_for((size_t)M * N), 256, 0, st>>>(m->splitws, ks, ep.split_stride, out, (size_t)M * N);
+  if (rc == HP_OK) splitk_sum<<<grid_for((size_t)M * N / 4), 256, 0, st>>>(m->splitws, ks, ep.split_stride, out, (size_t)M * N);
   return rc;
 }
 
@@ -686,18 +725,21 @@ void colsum(const bf16* in, int ld, int rows, int cols, float* out, float* ws, c
   colsum_final<<<(cols + 31) / 32, 256, 0, st>>>(ws, chunks, cols, out);
 }
 
-// Hidden layers for rows [0, rows) whose ids are in `ids` (n valid) -> m->Hb2
-int forward_hidden(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
-  encode_bits<<<(rows + 7) / 8, dim3(32, 8), 0, st>>>(ids, n, rows, m->N, m->Kin, m->X);
+// Hidden layers for rows [0, rows) whose ids are in `ids` (n valid) -> m->Hb2; with `labels` (n
+// entries) set, they are staged into m->labels (-1 in the padding rows)
+int forward_hidden(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st,
+                   const int32_t* labels = nullptr) {
+  encode_bits<<<(rows + 7) / 8, dim3(32, 8), 0, st>>>(ids, n, rows, m->N, m->Kin, m->X, labels,
+                                                      labels ? m->labels : nullptr);
   int rc = gemm(m->X, m->Kin, m->w1b, m->Kin, rows, m->H1, m->Kin, m->w[1], 1, nullptr, 0, m->Hb1, m->H1, st, m->tc_err);
   if (rc == HP_OK)
     rc = gemm(m->Hb1, m->H1, m->w2b, m->H1, rows, m->H2, m->H1, m->w[3], 1, nullptr, 0, m->Hb2, m->H2, st, m->tc_err);
   return rc;
 }
 
-// Forward pass: logits -> m->Z
-int forward(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st) {
-  int rc = forward_hidden(m, ids, n, rows, st);
+// Forward pass: logits -> m->Z (labels staged as in forward_hidden)
+int forward(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st, const int32_t* labels = nullptr) {
+  int rc = forward_hidden(m, ids, n, rows, st, labels);
   if (rc == HP_OK)
     rc = gemm(m->Hb2, m->H2, m->w3b, m->H2, rows, m->S, m->H2, m->w[5], 0, m->Z, m->Spad, nullptr, 0, st, m->tc_err);
   return rc;
@@ -758,7 +800,7 @@ int backward_tc(hp_mlp* m, int rows, cudaStream_t st, const AdamStep* adam) {
                             (S + 63) / 64, kSplitK);
     ep.split_stride = (size_t)rows * H2;
     rc = hp::tc_gemm(m->dZ, Spad, m->w3b, H2, rows, H2, S, ep, m->tc_err, st);
-    splitk_relu_backward<<<grid_for((size_t)rows * H2), 256, 0, st>>>(m->splitws, ep.ksplit, ep.split_stride, m->Hb2,
+    splitk_relu_backward<<<grid_for((size_t)rows * H2 / 4), 256, 0, st>>>(m->splitws, ep.ksplit, ep.split_stride, m->Hb2,
                                                                       m->dA2, (size_t)rows * H2);
   }
   {
@@ -805,14 +847,14 @@ int backward_tc(hp_mlp* m, int rows, cudaStream_t st, const AdamStep* adam) {
 // epilogue: a first pass of the layer's GEMM keeps per-row maxima and sums of exponentials, a
 // second pass recomputes the logits and writes their gradient (and its 32-row column sums), so
 // the fp32 logits never reach memory.
-int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st,
+int loss_and_gradients(hp_mlp* m, const unsigned long long* ids, const int32_t* labels, int n, int rows, cudaStream_t st,
                        const AdamStep* adam = nullptr) {
   if (!tc_enabled()) {
-    int rc = forward(m, ids, n, rows, st);
+    int rc = forward(m, ids, n, rows, st, labels);
     if (rc == HP_OK) rc = backward_legacy(m, n, rows, st);
     return rc;
   }
-  int rc = forward_hidden(m, ids, n, rows, st);
+  int rc = forward_hidden(m, ids, n, rows, st, labels);
   hp::TcEpilogue ea;
   ea.kt = -1;
   ea.bias = m->w[5];
@@ -1020,9 +1062,7 @@ extern "C" int hp_mlp_gradients(hp_mlp* m, const uint64_t* d_ids, const int32_t*
   if (n < 1 || n > m->max_batch) return hp::fail(HP_EINVAL, "hp_mlp_gradients: batch exceeds max_batch");
   cudaStream_t st = (cudaStream_t)stream;
   const int rows = round_up(n, 32);
-  cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
-  cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
-  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st);
+  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), d_labels, n, rows, st);
   if (rc != HP_OK) return rc;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_gradients: launch");
@@ -1053,22 +1093,30 @@ extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t
   if (n < 1 || n > m->max_batch) return hp::fail(HP_EINVAL, "hp_mlp_train_step: batch exceeds max_batch");
   cudaStream_t st = (cudaStream_t)stream;
   const int rows = round_up(n, 32);
-  cudaMemsetAsync(m->labels, 0xFF, (size_t)rows * 4, st);
-  cudaMemcpyAsync(m->labels, d_labels, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
   const int step = m->steps + 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const AdamStep adam{lr, b1, b2, eps, 1.f / (1.f - powf(b1, (float)step)), 1.f / (1.f - powf(b2, (float)step))};
   // on the tcgen05 path W3's update is fused into the GEMM that forms its gradient
   const bool fused = tc_enabled();
-  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), n, rows, st, fused ? &adam : nullptr);
+  int rc = loss_and_gradients(m, reinterpret_cast<const unsigned long long*>(d_ids), d_labels, n, rows, st,
+                              fused ? &adam : nullptr);
   if (rc != HP_OK) return rc;
   m->steps = step;
   // the weight matrices' bf16 copies are written by the update itself
   bf16* const wb[6] = {m->w1b, nullptr, m->w2b, nullptr, m->w3b, nullptr};
+  AdamSet set{};
+  size_t total = 0;
   for (int i = 0; i < 6; i++)
-    if (!(fused && i == 4))
-      adam_update<<<grid_for(m->n[i]), 256, 0, st>>>(m->w[i], m->g[i], m->m[i], m->v[i], wb[i], m->n[i], adam.lr, adam.b1,
-                                                       adam.b2, adam.eps, adam.c1, adam.c2);
+    if (!(fused && i == 4)) {
+      const int t = set.count++;
+      set.w[t] = m->w[i];
+      set.g[t] = m->g[i];
+      set.m[t] = m->m[i];
+      set.v[t] = m->v[i];
+      set.wb[t] = wb[i];
+      set.end[t] = total += m->n[i];
+    }
+  adam_update<<<grid_for(total), 256, 0, st>>>(set, adam.lr, adam.b1, adam.b2, adam.eps, adam.c1, adam.c2);
   refresh_copies(m, st, false);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_train_step: launch");

@@ -472,27 +472,10 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
       }
     };
     if (KT != 0 && (int)blockIdx.x < p.units) fetch_bias(unit_of(p, blockIdx.x).nb * TN);
-    // Adam epilogue: this warp's rows of the weights and moments of unit u's tile (one row per
-    // lane, its 128 columns) are prefetched into L2 a tile ahead of their use
-    auto prefetch_adam = [&](int u) {
-      if constexpr (KT == 0) {
-        if (!ep.adam_w || u >= p.units) return;
-        const Unit w = unit_of(p, u);
-        const int row = w.m0 + q * 32 + lane, col = w.nb * TN + cbeg;
-        if (row >= p.M || col >= p.N) return;
-        const uint32_t bytes = (uint32_t)min(CW, p.N - col) * 4u;
-        const size_t off = (size_t)row * ep.ldcf + col;
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ep.adam_w + off), "r"(bytes) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ep.adam_m + off), "r"(bytes) : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ep.adam_v + off), "r"(bytes) : "memory");
-      }
-    };
-    prefetch_adam(blockIdx.x);
     uint32_t tl = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
       const Unit w = unit_of(p, u);
-      prefetch_adam(u + gridDim.x);
       const int rbase = w.m0 + q * 32;  // first row of this warp
       // top-k mode: one running list per row over this warp's columns of all tiles of the unit,
       // ordered by (value descending, id ascending)
@@ -533,6 +516,25 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
       }
       for (int tn = w.nb; tn < w.ne; tn++, tl++) {
         const uint32_t a = tl & 1, ar = tl >> 1;
+        // store mode with a ReLU mask: bit r of keepm[i] says whether row rbase + r of this lane's
+        // column in chunk i is kept; loaded while the tile's MMAs run
+        uint32_t keepm[KT == 0 ? CW / 32 : 1];
+        if constexpr (KT == 0) {
+          const int rmax = min(32, p.M - rbase);
+#pragma unroll
+          for (int i = 0; i < CW / 32; i++) {
+            const int cl = tn * TN + cbeg + 32 * i + lane;
+            uint32_t keep = ~0u;
+            if (ep.relu_mask && cl < p.N) {
+              keep = 0u;
+#pragma unroll
+              for (int r = 0; r < 32; r++)
+                if (r < rmax && __bfloat162float(__ldg(ep.relu_mask + (size_t)(rbase + r) * ep.ldmask + cl)) > 0.f)
+                  keep |= 1u << r;
+            }
+            keepm[i] = keep;
+          }
+        }
         if (!wait_or_abort(&tmem_full[a], ar & 1, abort_flag, err, p.spin)) {
           ok = false;
           break;
@@ -694,11 +696,15 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
                     ep.wt[(size_t)(n0 + c0 + j) * ep.ldwt + rbase + lane] = __float2bfloat16(area[lane * 33 + j]);
                 }
               } else if (cl < p.N) {
+                uint32_t keep = keepm[0];  // this chunk's mask bits (~0 without a mask)
+#pragma unroll
+                for (int i = 1; i < CW / 32; i++)
+                  if (c0 - cbeg == 32 * i) keep = keepm[i];
                 for (int r = 0; r < rmax; r++) {
                   const size_t row = (size_t)(rbase + r);
                   float x = area[r * 33 + lane] + bl;
                   if (ep.relu) x = fmaxf(x, 0.f);
-                  if (ep.relu_mask && !(__bfloat162float(ep.relu_mask[row * ep.ldmask + cl]) > 0.f)) x = 0.f;
+                  if (!((keep >> r) & 1u)) x = 0.f;
                   if (ep.Cf) ep.Cf[(size_t)w.ks * ep.split_stride + row * ep.ldcf + cl] = x;
                   if (ep.Cb) ep.Cb[row * ep.ldcb + cl] = __float2bfloat16(x);
                 }
