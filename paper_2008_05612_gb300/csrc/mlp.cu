@@ -291,6 +291,8 @@ __global__ void cast_bf16(const float* __restrict__ in, bf16* __restrict__ out, 
 // lab_out set, also lab_out[b] = lab_in[b] for b < n and -1 for the padding rows
 __global__ void encode_bits(const unsigned long long* __restrict__ ids, int n, int rows, int N, int Kin, bf16* __restrict__ X,
                             const int32_t* __restrict__ lab_in, int32_t* __restrict__ lab_out) {
+  hp::pdl_wait();
+  hp::pdl_trigger();
   const int b = blockIdx.x * blockDim.y + threadIdx.y;
   if (b >= rows) return;
   if (lab_out && threadIdx.x == 0) lab_out[b] = b < n ? lab_in[b] : -1;
@@ -380,6 +382,8 @@ __global__ void softmax_xent(const float* __restrict__ Z, int ldz, int S, const 
 // chunk, two columns per thread from bf16 pairs), then out[c] = sum of part[., c] in chunk order.
 constexpr int kColChunk = 32;
 __global__ void colsum_partial(const bf16* __restrict__ in, int ld, int rows, int cols, float* __restrict__ part) {
+  hp::pdl_wait();
+  hp::pdl_trigger();
   const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (c >= cols) return;
   const int r0 = blockIdx.y * kColChunk, r1 = min(rows, r0 + kColChunk);
@@ -400,6 +404,8 @@ __global__ void colsum_partial(const bf16* __restrict__ in, int ld, int rows, in
 // 32 columns per block (lane = column): warp w sums the chunks w, w + 8, ... in order, then the
 // eight warp sums are added in warp order
 __global__ void colsum_final(const float* __restrict__ part, int chunks, int cols, float* __restrict__ out) {
+  hp::pdl_wait();
+  hp::pdl_trigger();
   __shared__ float ws[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
@@ -419,6 +425,8 @@ __global__ void colsum_final(const float* __restrict__ part, int chunks, int col
 // out = the sum of the split-K partial products (fp32), slices added in order; four elements per
 // thread and step (n and stride multiples of 4, 16-byte aligned buffers)
 __global__ void splitk_sum(const float* __restrict__ part, int splits, size_t stride, float* __restrict__ out, size_t n) {
+  hp::pdl_wait();
+  hp::pdl_trigger();
   for (size_t i = 4 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x); i < n; i += 4 * (size_t)gridDim.x * blockDim.x) {
     float4 v = __ldcs(reinterpret_cast<const float4*>(part + i));
     for (int k = 1; k < splits; k++) {
@@ -436,6 +444,8 @@ __global__ void splitk_sum(const float* __restrict__ part, int splits, size_t st
 // step as above
 __global__ void splitk_relu_backward(const float* __restrict__ part, int splits, size_t stride, const bf16* __restrict__ H,
                                      bf16* __restrict__ dA, size_t n) {
+  hp::pdl_wait();
+  hp::pdl_trigger();
   for (size_t i = 4 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x); i < n; i += 4 * (size_t)gridDim.x * blockDim.x) {
     float4 v = __ldcs(reinterpret_cast<const float4*>(part + i));
     for (int k = 1; k < splits; k++) {
@@ -486,6 +496,8 @@ struct AdamSet {
 };
 
 __global__ void adam_update(AdamSet s, float lr, float b1, float b2, float eps, float c1, float c2) {
+  hp::pdl_wait();
+  hp::pdl_trigger();
   const size_t n = s.end[s.count - 1];
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     int t = 0;
@@ -715,22 +727,24 @@ int weight_grad(hp_mlp* m, const bf16* dA, int lda, const bf16* H, int ldb, int 
   ep.ksplit = ks;
   ep.split_stride = (size_t)M * N;
   const int rc = hp::tc_gemm(dA, lda, H, ldb, M, N, K, ep, m->tc_err, st);
-  if (rc == HP_OK) splitk_sum<<<grid_for((size_t)M * N / 4), 256, 0, st>>>(m->splitws, ks, ep.split_stride, out, (size_t)M * N);
+  if (rc == HP_OK)
+    hp::launch_pdl(splitk_sum, dim3(grid_for((size_t)M * N / 4)), dim3(256), 0, st, m->splitws, ks, ep.split_stride, out,
+                   (size_t)M * N);
   return rc;
 }
 
 void colsum(const bf16* in, int ld, int rows, int cols, float* out, float* ws, cudaStream_t st) {
   const int chunks = (rows + kColChunk - 1) / kColChunk;
-  colsum_partial<<<dim3((cols + 255) / 256, chunks), 128, 0, st>>>(in, ld, rows, cols, ws);
-  colsum_final<<<(cols + 31) / 32, 256, 0, st>>>(ws, chunks, cols, out);
+  hp::launch_pdl(colsum_partial, dim3((cols + 255) / 256, chunks), dim3(128), 0, st, in, ld, rows, cols, ws);
+  hp::launch_pdl(colsum_final, dim3((cols + 31) / 32), dim3(256), 0, st, (const float*)ws, chunks, cols, out);
 }
 
 // Hidden layers for rows [0, rows) whose ids are in `ids` (n valid) -> m->Hb2; with `labels` (n
 // entries) set, they are staged into m->labels (-1 in the padding rows)
 int forward_hidden(hp_mlp* m, const unsigned long long* ids, int n, int rows, cudaStream_t st,
                    const int32_t* labels = nullptr) {
-  encode_bits<<<(rows + 7) / 8, dim3(32, 8), 0, st>>>(ids, n, rows, m->N, m->Kin, m->X, labels,
-                                                      labels ? m->labels : nullptr);
+  hp::launch_pdl(encode_bits, dim3((rows + 7) / 8), dim3(32, 8), 0, st, ids, n, rows, m->N, m->Kin, m->X, labels,
+                 labels ? m->labels : nullptr);
   int rc = gemm(m->X, m->Kin, m->w1b, m->Kin, rows, m->H1, m->Kin, m->w[1], 1, nullptr, 0, m->Hb1, m->H1, st, m->tc_err);
   if (rc == HP_OK)
     rc = gemm(m->Hb1, m->H1, m->w2b, m->H1, rows, m->H2, m->H1, m->w[3], 1, nullptr, 0, m->Hb2, m->H2, st, m->tc_err);
@@ -790,7 +804,7 @@ int backward_tc(hp_mlp* m, int rows, cudaStream_t st, const AdamStep* adam) {
   const int S = m->S, H1 = m->H1, H2 = m->H2, Kin = m->Kin, Spad = m->Spad;
   // layer 3: b3, then dH2 = dZ W3 (rows x H2 with an S-long contraction: too few tiles for the
   // GPU, so split K), then W3's gradient dZ^T H2 (stored or applied)
-  colsum_final<<<(S + 31) / 32, 256, 0, st>>>(m->colws, rows / 32, S, m->g[5]);
+  hp::launch_pdl(colsum_final, dim3((S + 31) / 32), dim3(256), 0, st, (const float*)m->colws, rows / 32, S, m->g[5]);
   {
     hp::TcEpilogue ep;
     ep.b_mn = true;
@@ -800,8 +814,8 @@ int backward_tc(hp_mlp* m, int rows, cudaStream_t st, const AdamStep* adam) {
                             (S + 63) / 64, kSplitK);
     ep.split_stride = (size_t)rows * H2;
     rc = hp::tc_gemm(m->dZ, Spad, m->w3b, H2, rows, H2, S, ep, m->tc_err, st);
-    splitk_relu_backward<<<grid_for((size_t)rows * H2 / 4), 256, 0, st>>>(m->splitws, ep.ksplit, ep.split_stride, m->Hb2,
-                                                                      m->dA2, (size_t)rows * H2);
+    hp::launch_pdl(splitk_relu_backward, dim3(grid_for((size_t)rows * H2 / 4)), dim3(256), 0, st, (const float*)m->splitws,
+                   ep.ksplit, ep.split_stride, (const bf16*)m->Hb2, m->dA2, (size_t)rows * H2);
   }
   {
     hp::TcEpilogue ep;
@@ -1116,7 +1130,8 @@ extern "C" int hp_mlp_train_step(hp_mlp* m, const uint64_t* d_ids, const int32_t
       set.wb[t] = wb[i];
       set.end[t] = total += m->n[i];
     }
-  adam_update<<<grid_for(total), 256, 0, st>>>(set, adam.lr, adam.b1, adam.b2, adam.eps, adam.c1, adam.c2);
+  hp::launch_pdl(adam_update, dim3(grid_for(total)), dim3(256), 0, st, set, adam.lr, adam.b1, adam.b2, adam.eps, adam.c1,
+                 adam.c2);
   refresh_copies(m, st, false);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return hp::cuda_fail(e, "hp_mlp_train_step: launch");

@@ -358,6 +358,10 @@ __global__ void __launch_bounds__(Shape<KT>::kThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // the set-up above touched no global memory; everything below may read the previous kernel's
+  // results
+  pdl_wait();
+  pdl_trigger();
   const uint32_t tmem = tmem_base;
   unsigned* err = p.err;
 
@@ -818,6 +822,8 @@ __global__ void topk_merge_kernel(const float* __restrict__ cv, const int32_t* _
 __global__ void softmax_finish_kernel(const float* __restrict__ stats, int lists, int rows, const int32_t* __restrict__ labels,
                                       const float* __restrict__ zlab, float* __restrict__ row_m, float* __restrict__ row_inv,
                                       float* __restrict__ loss) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   const bool row_ok = r < rows;  // whole warps past the last row still meet the block barrier below
   float m = -INFINITY, s = 0.f;
@@ -913,7 +919,7 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mdz
   static_assert(Shape<KT>::kSmem <= 227 * 1024, "shared memory of the tcgen05 GEMM");
   cudaFuncSetAttribute(gemm_tc_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<KT>::kSmem);
   const int grid = std::min(p.units, sm_count());
-  gemm_tc_kernel<KT><<<grid, Shape<KT>::kThreads, Shape<KT>::kSmem, st>>>(ma, mb, mdz, p);
+  launch_pdl(gemm_tc_kernel<KT>, dim3(grid), dim3(Shape<KT>::kThreads), Shape<KT>::kSmem, st, ma, mb, mdz, p);
 }
 
 }  // namespace
@@ -975,7 +981,8 @@ int tc_gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
 
 void tc_softmax_finish(const float* stats, int lists, int rows, const int32_t* labels, const float* zlab, float* row_m,
                        float* row_inv, float* loss, cudaStream_t st) {
-  softmax_finish_kernel<<<(rows + 7) / 8, 256, 0, st>>>(stats, lists, rows, labels, zlab, row_m, row_inv, loss);
+  launch_pdl(softmax_finish_kernel, dim3((rows + 7) / 8), dim3(256), 0, st, stats, lists, rows, labels, zlab, row_m, row_inv,
+             loss);
 }
 
 void tc_topk_merge(const float* cand_v, const int32_t* cand_i, int tiles, int rows, int kt, int k, int S, int32_t* out,

@@ -10,8 +10,32 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 namespace hp {
+
+// Programmatic dependent launch.  A kernel started by launch_pdl may begin (be scheduled, run its
+// set-up) while the kernel before it on the stream is still running; it calls pdl_wait() before
+// its first access to global memory, which returns once that kernel has completed and its writes
+// are visible, and then pdl_trigger(), which lets the next such kernel be scheduled.  Kernels that
+// call them behave as usual under an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 constexpr int kTcTileM = 128, kTcTileN = 256;
 constexpr int kTcStatsListsPerTile = 4;  // row-statistics mode: lists per row and tile range
