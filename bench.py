@@ -371,21 +371,22 @@ def small_boxes_and_batch(hp, torch, reps: int = 3):
 PROPOSAL_ROWS = 16384  # ids per proposal chunk (the network's max_batch)
 
 
-def proposal_params(N, S):
+def proposal_params(N, S, H: int = 512):
     from paper_2008_05612_gb300 import inputs
 
-    return [inputs.init_weights((512, N), N, 61), inputs.init_weights((512,), N, 62),
-            inputs.init_weights((512, 512), 512, 63), inputs.init_weights((512,), 512, 64),
-            inputs.init_weights((S, 512), 512, 65), inputs.init_weights((S,), 512, 66)]
+    return [inputs.init_weights((H, N), N, 61), inputs.init_weights((H,), N, 62),
+            inputs.init_weights((H, H), H, 63), inputs.init_weights((H,), H, 64),
+            inputs.init_weights((S, H), H, 65), inputs.init_weights((S,), H, 66)]
 
 
-def train_proposal(hp, s, torch, tids, tlab, epochs: float = 1.0, batch: int = 4096, lr: float = 1e-3):
-    """N -> 512 -> 512 -> S network trained on the GPU with the library's kernels (one Adam step per batch
-    of `batch` (id, label) pairs, `epochs` passes over the training set); returns (trained, untrained, info)."""
+def train_proposal(hp, s, torch, tids, tlab, epochs: float = 1.0, batch: int = 4096, lr: float = 1e-3, width: int = 512):
+    """N -> width -> width -> S network trained on the GPU with the library's kernels (one Adam step per
+    batch of `batch` (id, label) pairs, `epochs` passes over the training set); returns (trained, untrained,
+    info)."""
     N, S = s.N, s.S
-    params = proposal_params(N, S)
-    net = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
-    untrained = hp.MLP(N, 512, 512, S, PROPOSAL_ROWS, params)
+    params = proposal_params(N, S, width)
+    net = hp.MLP(N, width, width, S, PROPOSAL_ROWS, params)
+    untrained = hp.MLP(N, width, width, S, PROPOSAL_ROWS, params)
     steps = max(1, int(epochs * tids.numel() / batch))
     gen = torch.Generator(device="cuda").manual_seed(0)
     perm = torch.randperm(tids.numel(), device="cuda", generator=gen)
@@ -407,9 +408,10 @@ def train_proposal(hp, s, torch, tids, tlab, epochs: float = 1.0, batch: int = 4
     return net, untrained, info
 
 
-def compare_on_ids(hp, s, torch, ev, models, k: int = 4):
+def compare_on_ids(hp, s, torch, ev, models, k: int = 4, plain=None):
     """Plain per-sequence scan vs (network top-k + candidate expansion + pruned scan) on the same ids,
-    CUDA-event timed (1 warm-up + 3 calls); phenotypes must agree exactly."""
+    CUDA-event timed (1 warm-up + 3 calls); phenotypes must agree exactly.  With `plain` (the plain
+    scan's phenotypes of `ev`) given, the plain scan is not run again."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n = ev.numel()
 
@@ -423,8 +425,10 @@ def compare_on_ids(hp, s, torch, ev, models, k: int = 4):
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1) / reps
 
-    plain, ms_plain = timed(lambda: hp.sequence_scan(s, ev))
-    res = {"plain_per_sequence": {"ms": ms_plain, "sequences_per_s": n / (ms_plain * 1e-3)}}
+    res = {}
+    if plain is None:
+        plain, ms_plain = timed(lambda: hp.sequence_scan(s, ev))
+        res["plain_per_sequence"] = {"ms": ms_plain, "sequences_per_s": n / (ms_plain * 1e-3)}
     for name, model in models.items():
         cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
 
@@ -467,9 +471,9 @@ def learned_full_space(hp, s, torch, net, phen, k: int = 4, chunk: int = 1 << 20
             "exact_eval_fraction": int(cnt[0]) / (total * s.S_dir), "mismatches_vs_exhaustive_map": int(mism.item())}
 
 
-def learned_leg(hp, s, torch, full_space: bool = True, eval_n: int = 1 << 16, k: int = 4):
-    """3x3x3: labels = the lowest-index minimiser (aux output) of the exhaustive kernel's full map on the
-    seeded 1-in-10 sample of the space; evaluation on `eval_n` seeded ids and on the whole space."""
+def labels_3x3x3(hp, s, torch):
+    """The exhaustive map of the box, its CUDA-event time, and the training set: the seeded 1-in-10
+    sample of the space labelled with the lowest-index minimiser (aux output) of the map kernel."""
     from paper_2008_05612_gb300 import inputs
 
     N = s.N
@@ -486,7 +490,16 @@ def learned_leg(hp, s, torch, full_space: bool = True, eval_n: int = 1 << 16, k:
     del ids_all
     tids = torch.from_numpy(train_ids.view(np.int64)).to("cuda")
     tlab = aux[tids]
-    del aux
+    return phen, ms_map, tids, tlab
+
+
+def learned_leg(hp, s, torch, full_space: bool = True, eval_n: int = 1 << 16, k: int = 4):
+    """3x3x3: labels = the lowest-index minimiser (aux output) of the exhaustive kernel's full map on the
+    seeded 1-in-10 sample of the space; evaluation on `eval_n` seeded ids and on the whole space."""
+    from paper_2008_05612_gb300 import inputs
+
+    N = s.N
+    phen, ms_map, tids, tlab = labels_3x3x3(hp, s, torch)
     net, untrained, info = train_proposal(hp, s, torch, tids, tlab)
     del tids, tlab
     ev = torch.from_numpy(inputs.sample_ids(N, eval_n, seed=123).view(np.int64)).to("cuda")
@@ -497,6 +510,27 @@ def learned_leg(hp, s, torch, full_space: bool = True, eval_n: int = 1 << 16, k:
     if full_space:
         out["full_space"] = learned_full_space(hp, s, torch, net, phen, k)
     return out
+
+
+def proposal_sweep(hp, s, torch, settings=((128, 1.0), (256, 1.0), (512, 1.0), (512, 3.0)), ks=(1, 2, 4, 8, 16),
+                   eval_n: int = 1 << 16):
+    """3x3x3 learned proposal: hidden width and training epochs (`settings`) against top-k (`ks`); per
+    setting the pruned scan's time, proposal time, exact-evaluation fraction and mismatches on `eval_n`
+    seeded ids (one JSON line each, then the plain scan's line)."""
+    from paper_2008_05612_gb300 import inputs
+
+    _, _, tids, tlab = labels_3x3x3(hp, s, torch)
+    ev = torch.from_numpy(inputs.sample_ids(s.N, eval_n, seed=123).view(np.int64)).to("cuda")
+    base = compare_on_ids(hp, s, torch, ev, {}, 4)
+    plain = hp.sequence_scan(s, ev)
+    for width, epochs in settings:
+        net, _, info = train_proposal(hp, s, torch, tids, tlab, epochs=epochs, width=width)
+        for k in ks:
+            res = compare_on_ids(hp, s, torch, ev, {"learned_pruned": net}, k, plain=plain)["learned_pruned"]
+            print(json.dumps({"box": "3x3x3", "width": width, "epochs": epochs, "topk": k, "train_s": info["train_s"],
+                              "loss_last": info["loss_last"], **res}), flush=True)
+        del net
+    print(json.dumps({"box": "3x3x3", "eval_ids": eval_n, **base}), flush=True)
 
 
 def learned_leg_6x6(hp, torch, n_train: int = 13_421_773, eval_per_shard: int = 1 << 15, shards: int = 2, k: int = 4):
@@ -543,6 +577,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (one JSON line)")
+    ap.add_argument("--proposal-sweep", action="store_true",
+                    help="3x3x3 proposal network: hidden width, epochs and top-k against the pruned scan's cost")
     ap.add_argument("--stream", default=None, metavar="BOX:BITS[:WINDOW[:DIR]]",
                     help="whole-space map of BOX in 2^BITS shards with exact designability and Eq. 2 statistics")
     ap.add_argument("--stream-components", default=None, metavar="BOX:BITS[:WINDOW]",
@@ -590,6 +626,9 @@ def main():
 
     s = hp.Structs(DIMS)
     N, S, Sdir = s.N, s.S, s.S_dir
+    if args.proposal_sweep:
+        proposal_sweep(hp, s, torch)
+        return 0
     if args.learned_only:
         print(json.dumps({"metric": METRIC, "learned": {"3x3x3": learned_leg(hp, s, torch),
                                                          "6x6": learned_leg_6x6(hp, torch)}}))
