@@ -120,3 +120,28 @@ def test_histogram_outputs_are_checked_before_any_launch():
         with pytest.raises(hp.HPError) as e:
             fn(phen, 0, short)
         assert e.value.code == hp.HP_EINVAL
+
+
+def test_every_dependent_launch_waits_for_its_predecessor():
+    """A kernel started by launch_pdl may run while the kernel before it is still running, so its
+    body must execute pdl_wait() before it touches global memory: the simple kernels as their first
+    statement, the tcgen05 GEMM right after its shared-memory and tensor-memory set-up."""
+    import re
+
+    csrc = os.path.join(os.path.dirname(hp.__file__), "csrc")
+    text = "".join(open(os.path.join(csrc, f)).read() for f in sorted(os.listdir(csrc)) if f.endswith(".cu"))
+    launched = set(re.findall(r"launch_pdl\(\s*([A-Za-z_]\w*)", text))
+    assert {"gemm_tc_kernel", "softmax_finish_kernel", "encode_bits", "adam_update"} <= launched, launched
+    for name in launched:
+        m = re.search(r"__global__[^;{]*?\b" + name + r"\s*\([^)]*\)\s*\{", text, re.S)
+        assert m, name
+        body = text[m.end():]
+        if name == "gemm_tc_kernel":
+            setup, rest = body.split("pdl_wait();", 1)
+            # the set-up allocates tensor memory, initialises barriers and prefetches the tensor
+            # maps; it reads no global memory
+            for access in ("ep.", "p.err", "__ldg", "ld.global", "cp.async.bulk.tensor"):
+                assert access not in setup, (name, access)
+        else:
+            first = body.lstrip().split(";", 1)[0]
+            assert first.replace("hp::", "") == "pdl_wait()", (name, first)
